@@ -1,0 +1,230 @@
+/*
+ * gj.h - C ABI of the GB300 joint gravity-magnetic inversion library.
+ *
+ * Implements the hot path of Vatankhah, Renaut, Huang, Mickus & Gharloghi,
+ * "Large-scale focusing joint inversion of gravity and magnetic data with
+ * Gramian constraint" (arXiv 2112.15562): the per-depth-layer BTTB sensitivity
+ * products A m and A^T r of the gravity and magnetic problems evaluated with 2-D
+ * FFTs of the BCCB embedding (Sec. 2.7.1), and the regularised reweighted CG
+ * joint solve with Lp stabilisers and the Gramian coupling (Eq. RRCG:1-8,
+ * Secs. 2.2-2.8).
+ *
+ * Conventions (all calls):
+ *  - Pointers are DEVICE pointers unless the comment says "host".  The caller
+ *    owns every buffer it passes; the library never frees caller memory.
+ *  - Vectors use the precision of the operator: double for GJ_FP64, float for
+ *    GJ_FP32_MIXED.  Scalars reported by the library are always double.
+ *  - Model vectors are layer-major m[r][iy][ix] (ix fastest, r = depth layer,
+ *    n = nx*ny*nz); data vectors are d[jy][jx] (s = sx*sy).  x = East,
+ *    y = North, z = Down.
+ *  - Calls are asynchronous on `stream` unless stated.  A gj_op owns a device
+ *    workspace, so calls that use the same gj_op must be ordered (one stream,
+ *    or explicit events); different gj_op objects are independent.
+ *  - Errors: argument checks run synchronously and return a negative
+ *    gj_status without enqueuing work; gj_last_error() then returns a message
+ *    (per thread).  CUDA launch failures return GJ_ERR_CUDA.
+ */
+#ifndef GJ_H
+#define GJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *gj_stream_t;
+
+typedef enum {
+    GJ_OK = 0,
+    GJ_ERR_ARG = -1,         /* invalid argument (message in gj_last_error) */
+    GJ_ERR_OOM = -2,         /* device allocation failed */
+    GJ_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed */
+    GJ_ERR_NONFINITE = -4,   /* the solver met a non-finite scalar */
+    GJ_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    GJ_ERR_UNSUPPORTED = -6  /* e.g. a padded size with a prime factor > 17 */
+} gj_status;
+
+typedef enum { GJ_GRAVITY = 1, GJ_MAGNETIC = 2 } gj_field;
+typedef enum { GJ_FP64 = 0, GJ_FP32_MIXED = 1 } gj_precision;
+
+/* Station grid and prism mesh (Sec. 2.7.1).  Prism (r, iy, ix) spans
+ * [ix*dx, (ix+1)*dx] x [iy*dy, (iy+1)*dy] x [z_edges[r], z_edges[r+1]];
+ * station (jy, jx) sits at the horizontal centre of prism column
+ * (jy + off_y, jx + off_x) at depth station_z, which must not lie below
+ * z_edges[0] (stations at or above the top of the mesh). */
+typedef struct {
+    int sx, sy;              /* stations in x and y */
+    int nx, ny, nz;          /* prisms in x, y and depth layers */
+    double dx, dy;           /* cell sizes, metres */
+    const double *z_edges;   /* host, nz + 1 increasing depths, metres */
+    double station_z;        /* station depth, metres (0 = top of the mesh) */
+    int off_x, off_y;        /* prism columns left of / below the first station */
+} gj_grid;
+
+/* Inducing field for the total-field anomaly with induced magnetisation only
+ * (Sec. 2.1: no remanence, no self-demagnetisation). */
+typedef struct {
+    double F_nT;             /* intensity, nT */
+    double incl_deg;         /* inclination, degrees, positive down */
+    double decl_deg;         /* declination, degrees east of north */
+} gj_mag;
+
+typedef struct gj_op gj_op;  /* opaque: one field's operator, its spectra and workspace */
+
+typedef struct {
+    int sx, sy, nx, ny, nz;
+    int Nx, Ny;              /* padded BCCB sizes in use */
+    int ncol;                /* stored spectrum columns, Nx/2 + 1 */
+    gj_field field;
+    gj_precision precision;
+    int64_t spectrum_bytes;  /* device bytes of the stored layer spectra */
+    int64_t workspace_bytes; /* device bytes of the per-op workspace */
+} gj_op_info_t;
+
+/*
+ * gj_bttb_setup - build one field's operator (Sec. 2.7.1, Eq. d=gm).
+ *
+ * Evaluates, in FP64 on the device, the closed-form prism field (vertical
+ * gravity in mGal per g/cc, or total-field anomaly in nT per SI unit) for
+ * every station-minus-prism offset of each depth layer, embeds each layer's
+ * table T_r in an Ny x Nx circulant array (T[c mod N] = K(c + off) for
+ * c in [-(n-1), s-1]), and keeps its 2-D FFT (scaled by 1/(Nx Ny)) in the
+ * operator's precision.  Npad_y/Npad_x = 0 selects the smallest size
+ * >= s + n - 1 whose prime factors are all <= 7; otherwise each must be
+ * >= s + n - 1 with prime factors <= 17 (any such size gives the same
+ * product).  `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
+ * Synchronous with respect to the host on return (the op is ready).
+ * Returns GJ_ERR_ARG for invalid sizes, GJ_ERR_UNSUPPORTED for a padded size
+ * above 4096 or with a larger prime factor, GJ_ERR_OOM if device memory runs
+ * out.  On success *out owns device memory until gj_op_destroy.
+ */
+gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag,
+                        gj_precision precision, int Npad_y, int Npad_x,
+                        gj_stream_t stream, gj_op **out);
+
+/* Sizes of an operator (host struct filled synchronously). */
+gj_status gj_op_info(const gj_op *op, gj_op_info_t *info);
+
+/* Frees an operator (waits for the device to finish using it).  NULL is a no-op. */
+void gj_op_destroy(gj_op *op);
+
+/*
+ * gj_g_forward - d = A m for one field (Eq. d=gm): the sum over depth layers
+ * of IFFT2(FFT2(T_r) . FFT2(X_r)) cropped to the station block, where X_r is
+ * layer r of m in the upper-left corner of an Ny x Nx zero array
+ * (Sec. 2.7.1).  m: n values, d: s values, both of the op's precision;
+ * m and d must not overlap.
+ */
+gj_status gj_g_forward(const gj_op *op, const void *m, void *d, gj_stream_t stream);
+
+/*
+ * gj_g_adjoint - g = A^T r for one field: per layer,
+ * IFFT2(conj(FFT2(T_r)) . FFT2(V)) cropped to the prism block, V = r in the
+ * upper-left corner (Sec. 2.7.1).  r: s values, g: n values.
+ */
+gj_status gj_g_adjoint(const gj_op *op, const void *r, void *g, gj_stream_t stream);
+
+/*
+ * gj_gramian_value_grad - the Gramian coupling (Eq. Gramian, RRCG:2-3).
+ * S = (m1,m1)(m2,m2) - (m1,m2)^2 written to the device double *S, and the
+ * ascent directions l1 = (m2,m2) m1 - (m1,m2) m2, l2 = (m1,m1) m2 - (m1,m2) m1
+ * (half the gradient of S).  l1 / l2 may be NULL to skip them.  Vectors of
+ * length n in the given precision; inner products accumulate in FP64.
+ */
+gj_status gj_gramian_value_grad(int64_t n, gj_precision precision,
+                                const void *m1, const void *m2, double *S,
+                                void *l1, void *l2, gj_stream_t stream);
+
+/* Solver options (Eq. RRCG:1-8; Secs. 2.5, 2.6, 2.8). Index 0 = gravity, 1 = magnetic. */
+enum { GJ_SCALARS_AUTO = 0, GJ_SCALARS_JOINT = 1, GJ_SCALARS_PER_FIELD = 2 };
+
+typedef struct {
+    int p[2];              /* Lp stabiliser, 1 (Eq. WL) or 2 (W_L = I, Sec. 3.1.5) */
+    double eps2;           /* focusing parameter eps^2 of Eq. WL (paper: 1e-9) */
+    double alpha1[2];      /* initial regularisation parameters */
+    double q[2];           /* decay of Eq. regpara */
+    double alpha_min[2];   /* lower bound on alpha (0 = none) */
+    double lambda[2];      /* Lagrange parameters of the Gramian term */
+    double lo[2], hi[2];   /* bounds of Sec. 2.5 */
+    int kmax;              /* maximum number of model updates */
+    int stop_on_chi2;      /* 1: stop once both fields pass Eq. chi2 */
+    int scalars;           /* GJ_SCALARS_*: AUTO = per field iff both lambdas are 0 */
+} gj_rrcg_params;
+
+typedef struct {
+    int status;            /* GJ_OK or GJ_ERR_NONFINITE */
+    int iterations;        /* model updates performed */
+    int converged;         /* 1 if both fields passed Eq. chi2 */
+    int satisfied[2];
+    double phi[2];         /* chi^2 misfit of the returned models */
+    double alpha[2];       /* regularisation parameters at the end */
+    double S_G;            /* Gramian of the returned models */
+} gj_rrcg_report;
+
+/* Per-iteration history record (optional). */
+typedef struct {
+    double phi[2], alpha[2], S_G, s[2], beta[2];
+} gj_rrcg_hist;
+
+/*
+ * gj_rrcg_joint_solve - joint RRCG solve of Eq. (GlobalFunction2) with the
+ * Gramian in the original space (Eq. RRCG:1-8), bounds (Sec. 2.5), the chi^2
+ * stop (Eq. chi2) and the alpha schedule (Eq. regpara).
+ *
+ * ops[0] is the gravity operator, ops[1] the magnetic one; both must have the
+ * same grid sizes, padded sizes and precision.  dobs[i], sigma[i]: s values
+ * (W_d = 1/sigma); w_depth[i]: nz per-layer depth weights; w_hard[i]: n values
+ * or NULL (identity); m_apr[i]: n values or NULL (zero).  m[i]: n values, the
+ * starting model on entry, the result on return.  hist: device array of
+ * kmax + 1 records or NULL.  *rep (host) is filled on return; the call
+ * synchronises `stream`.  Non-convergence by kmax is not an error
+ * (rep->converged = 0).
+ */
+gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrcg_params *params,
+                              const void *const dobs[2], const void *const sigma[2],
+                              const void *const m_apr[2], const void *const w_depth[2],
+                              const void *const w_hard[2], void *const m[2],
+                              gj_rrcg_hist *hist, gj_rrcg_report *rep, gj_stream_t stream);
+
+/* Stepwise form of the same solve: a solver object holds the state (search
+ * directions, scalars) and enqueues whole iterations without host round trips;
+ * the stop test runs on the device and later iterations become no-ops. */
+typedef struct gj_rrcg gj_rrcg;
+
+gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_params *params,
+                         const void *const dobs[2], const void *const sigma[2],
+                         const void *const m_apr[2], const void *const w_depth[2],
+                         const void *const w_hard[2], void *const m[2],
+                         gj_rrcg_hist *hist, gj_stream_t stream, gj_rrcg **out);
+/* Enqueue `iters` iterations (each: 2 forward and 1 adjoint product per field
+ * plus the fused vector updates).  use_graph = 1 replays one captured CUDA
+ * graph per iteration. */
+gj_status gj_rrcg_iterate(gj_rrcg *solver, int iters, int use_graph, gj_stream_t stream);
+/* Synchronises `stream` and fills *rep (host). */
+gj_status gj_rrcg_report_get(gj_rrcg *solver, gj_rrcg_report *rep, gj_stream_t stream);
+/* Synchronises `stream`; returns 1 once the device-side stop flag is set, 0 if
+ * not, -1 on error. */
+int gj_rrcg_done(gj_rrcg *solver, gj_stream_t stream);
+/* Kernel timing for roofline measurements: while enabled, a CUDA event pair is
+ * recorded on the launching stream around every launch of the spectrum
+ * multiply-and-sum column kernel (two per iteration).  Enabling it drops a graph
+ * captured without the events.  gj_rrcg_profile_read synchronises the device and
+ * returns the number of timed launches and their total milliseconds since the
+ * previous read (for graph replays: the launches of the last replay). */
+gj_status gj_rrcg_profile(gj_rrcg *solver, int enable);
+gj_status gj_rrcg_profile_read(gj_rrcg *solver, int *launches, double *total_ms);
+void gj_rrcg_destroy(gj_rrcg *solver);
+
+/* Last error message of the calling thread ("" if none). */
+const char *gj_last_error(void);
+
+/* Library version string. */
+const char *gj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H */

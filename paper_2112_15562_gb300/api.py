@@ -1,0 +1,271 @@
+"""Python-facing wrappers with the C-ABI names (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import check, load
+
+_PREC = {"fp64": L.GJ_FP64, "fp32": L.GJ_FP32_MIXED, L.GJ_FP64: L.GJ_FP64, L.GJ_FP32_MIXED: L.GJ_FP32_MIXED}
+_FIELD = {"gravity": L.GJ_GRAVITY, "magnetic": L.GJ_MAGNETIC, L.GJ_GRAVITY: L.GJ_GRAVITY,
+          L.GJ_MAGNETIC: L.GJ_MAGNETIC}
+
+
+def _stream(stream=None) -> ct.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[ct.c_void_p]:
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _vec(t: torch.Tensor, dtype, n: int, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {n} values")
+    return t
+
+
+def depth_weights(z_edges, beta: float) -> np.ndarray:
+    """Li & Oldenburg style depth weight per layer, (z_c / z_c,top)^(-beta/2) at the
+    layer centres (the form is not printed in the paper; top layer has weight 1)."""
+    z = np.asarray(z_edges, dtype=np.float64)
+    zc = 0.5 * (z[:-1] + z[1:])
+    return (zc / zc[0]) ** (-beta / 2.0)
+
+
+class Op:
+    """One field's BTTB operator (owns device spectra and workspace)."""
+
+    def __init__(self, handle: int, info: L.OpInfo):
+        self._h = ct.c_void_p(handle)
+        self.info = info
+        self.precision = info.precision
+        self.dtype = torch.float64 if info.precision == L.GJ_FP64 else torch.float32
+        self.n = info.nx * info.ny * info.nz
+        self.s = info.sx * info.sy
+
+    @property
+    def handle(self):
+        return self._h
+
+    def forward(self, m: torch.Tensor, d: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        return g_forward(self, m, d, stream)
+
+    def adjoint(self, r: torch.Tensor, g: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        return g_adjoint(self, r, g, stream)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().gj_op_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bttb_setup(grid, field, mag=None, precision="fp32", npad=(0, 0), stream=None) -> Op:
+    """gj_bttb_setup: ``grid`` has sx, sy, nx, ny, nz, dx, dy, z_edges[, station_z, off_x, off_y];
+    ``mag`` has F, incl, decl (magnetic only)."""
+    lib = load()
+    z = np.ascontiguousarray(np.asarray(grid.z_edges, dtype=np.float64))
+    g = L.Grid(int(grid.sx), int(grid.sy), int(grid.nx), int(grid.ny), int(grid.nz), float(grid.dx),
+               float(grid.dy), z.ctypes.data_as(ct.POINTER(ct.c_double)), float(getattr(grid, "station_z", 0.0)),
+               int(getattr(grid, "off_x", 0)), int(getattr(grid, "off_y", 0)))
+    m = None
+    if mag is not None:
+        m = L.Mag(float(mag.F), float(mag.incl), float(mag.decl))
+    out = ct.c_void_p()
+    check(lib.gj_bttb_setup(ct.byref(g), _FIELD[field], ct.byref(m) if m is not None else None,
+                            _PREC[precision], int(npad[0]), int(npad[1]), _stream(stream), ct.byref(out)))
+    info = L.OpInfo()
+    check(lib.gj_op_info(out, ct.byref(info)))
+    return Op(out.value, info)
+
+
+def g_forward(op: Op, m: torch.Tensor, d: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """gj_g_forward: d = A m."""
+    _vec(m, op.dtype, op.n, "m")
+    if d is None:
+        d = torch.empty(op.s, dtype=op.dtype, device=m.device)
+    _vec(d, op.dtype, op.s, "d")
+    check(load().gj_g_forward(op.handle, _ptr(m), _ptr(d), _stream(stream)))
+    return d
+
+
+def g_adjoint(op: Op, r: torch.Tensor, g: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """gj_g_adjoint: g = A^T r."""
+    _vec(r, op.dtype, op.s, "r")
+    if g is None:
+        g = torch.empty(op.n, dtype=op.dtype, device=r.device)
+    _vec(g, op.dtype, op.n, "g")
+    check(load().gj_g_adjoint(op.handle, _ptr(r), _ptr(g), _stream(stream)))
+    return g
+
+
+def gramian_value_grad(m1: torch.Tensor, m2: torch.Tensor, want_dirs: bool = True, stream=None):
+    """gj_gramian_value_grad: returns (S as a 1-element float64 CUDA tensor, l1, l2)."""
+    if m1.dtype not in (torch.float32, torch.float64) or m2.dtype != m1.dtype:
+        raise ValueError("m1 and m2 must share float32 or float64")
+    n = m1.numel()
+    _vec(m1, m1.dtype, n, "m1")
+    _vec(m2, m1.dtype, n, "m2")
+    prec = L.GJ_FP64 if m1.dtype == torch.float64 else L.GJ_FP32_MIXED
+    S = torch.empty(1, dtype=torch.float64, device=m1.device)
+    l1 = torch.empty_like(m1) if want_dirs else None
+    l2 = torch.empty_like(m2) if want_dirs else None
+    check(load().gj_gramian_value_grad(n, prec, _ptr(m1), _ptr(m2), _ptr(S), _ptr(l1), _ptr(l2), _stream(stream)))
+    return S, l1, l2
+
+
+def solver_params(p=(1, 1), eps2=1e-9, alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(0.0, 0.0),
+                  lam=(0.0, 0.0), lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=50, stop_on_chi2=True,
+                  scalars="auto") -> L.RRCGParams:
+    P = L.RRCGParams()
+    P.p[:] = [int(v) for v in p]
+    P.eps2 = float(eps2)
+    P.alpha1[:] = [float(v) for v in alpha1]
+    P.q[:] = [float(v) for v in q]
+    P.alpha_min[:] = [float(v) for v in alpha_min]
+    P.lambda_[:] = [float(v) for v in lam]
+    P.lo[:] = [float(v) for v in lo]
+    P.hi[:] = [float(v) for v in hi]
+    P.kmax = int(kmax)
+    P.stop_on_chi2 = 1 if stop_on_chi2 else 0
+    P.scalars = {"auto": L.GJ_SCALARS_AUTO, "joint": L.GJ_SCALARS_JOINT, "per_field": L.GJ_SCALARS_PER_FIELD}[scalars]
+    return P
+
+
+def _pair(vals, name, op, n, allow_none=False):
+    arr = (ct.c_void_p * 2)()
+    if vals is None:
+        if not allow_none:
+            raise ValueError(f"{name} is required")
+        return None
+    for i in range(2):
+        v = vals[i]
+        if v is None:
+            if not allow_none:
+                raise ValueError(f"{name}[{i}] is required")
+            arr[i] = None
+        else:
+            _vec(v, op.dtype, n, f"{name}[{i}]")
+            arr[i] = v.data_ptr()
+    return arr
+
+
+def _report(rep: L.RRCGReport) -> dict:
+    return {"status": rep.status, "iterations": rep.iterations, "converged": bool(rep.converged),
+            "satisfied": [bool(rep.satisfied[0]), bool(rep.satisfied[1])], "phi": list(rep.phi),
+            "alpha": list(rep.alpha), "S_G": rep.S_G}
+
+
+def _hist_rows(h: torch.Tensor, count: int):
+    a = h[:count].cpu().numpy()
+    return [{"phi": list(r[0:2]), "alpha": list(r[2:4]), "S_G": float(r[4]), "s": list(r[5:7]),
+             "beta": list(r[7:9])} for r in a]
+
+
+class Solver:
+    """Stepwise joint RRCG (gj_rrcg_create / iterate / report_get)."""
+
+    def __init__(self, ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_depth, m, m_apr=None,
+                 w_hard=None, history=False, stream=None):
+        lib = load()
+        self.ops = list(ops)
+        o = ops[0]
+        self._keep = [dobs, sigma, w_depth, m, m_apr, w_hard]
+        self.hist = None
+        if history:
+            self.hist = torch.zeros((params.kmax + 1, 9), dtype=torch.float64, device=m[0].device)
+        handles = (ct.c_void_p * 2)(ops[0].handle.value, ops[1].handle.value)
+        out = ct.c_void_p()
+        nz = o.info.nz
+        check(lib.gj_rrcg_create(handles, ct.byref(params), _pair(dobs, "dobs", o, o.s), _pair(sigma, "sigma", o, o.s),
+                                 _pair(m_apr, "m_apr", o, o.n, True), _pair(w_depth, "w_depth", o, nz),
+                                 _pair(w_hard, "w_hard", o, o.n, True), _pair(m, "m", o, o.n),
+                                 _ptr(self.hist), _stream(stream), ct.byref(out)))
+        self._h = out
+        self.kmax = params.kmax
+
+    def iterate(self, iters: int, use_graph: bool = True, stream=None):
+        check(load().gj_rrcg_iterate(self._h, int(iters), 1 if use_graph else 0, _stream(stream)))
+
+    def done(self, stream=None) -> bool:
+        d = load().gj_rrcg_done(self._h, _stream(stream))
+        if d < 0:
+            check(-3)
+        return bool(d)
+
+    def report(self, stream=None) -> dict:
+        rep = L.RRCGReport()
+        check(load().gj_rrcg_report_get(self._h, ct.byref(rep), _stream(stream)))
+        out = _report(rep)
+        if self.hist is not None:
+            out["history"] = _hist_rows(self.hist, out["iterations"] + 1)
+        return out
+
+    def profile(self, enable: bool = True):
+        check(load().gj_rrcg_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        n = ct.c_int()
+        ms = ct.c_double()
+        check(load().gj_rrcg_profile_read(self._h, ct.byref(n), ct.byref(ms)))
+        return n.value, ms.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().gj_rrcg_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rrcg_joint_solve(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_depth, m, m_apr=None, w_hard=None,
+                     history=False, stream=None) -> dict:
+    """gj_rrcg_joint_solve on device tensors; m (two tensors) is updated in place."""
+    lib = load()
+    o = ops[0]
+    hist = torch.zeros((params.kmax + 1, 9), dtype=torch.float64, device=m[0].device) if history else None
+    handles = (ct.c_void_p * 2)(ops[0].handle.value, ops[1].handle.value)
+    rep = L.RRCGReport()
+    check(lib.gj_rrcg_joint_solve(handles, ct.byref(params), _pair(dobs, "dobs", o, o.s),
+                                  _pair(sigma, "sigma", o, o.s), _pair(m_apr, "m_apr", o, o.n, True),
+                                  _pair(w_depth, "w_depth", o, o.info.nz), _pair(w_hard, "w_hard", o, o.n, True),
+                                  _pair(m, "m", o, o.n), _ptr(hist), ct.byref(rep), _stream(stream)))
+    out = _report(rep)
+    if hist is not None:
+        out["history"] = _hist_rows(hist, out["iterations"] + 1)
+    return out
+
+
+def rrcg_joint_solve_host(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_depth, m0, stream=None):
+    """The same solve with host (numpy) inputs: copies in, solves, copies the models out.
+    Returns (models as numpy arrays, report, bytes copied in, bytes copied out)."""
+    dt = ops[0].dtype
+    dev = torch.device("cuda")
+    pin = [torch.from_numpy(np.ascontiguousarray(x)).to(dt).pin_memory()
+           for x in list(dobs) + list(sigma) + list(w_depth) + list(m0)]
+    dv = [t.to(dev, non_blocking=True) for t in pin]
+    rep = rrcg_joint_solve(ops, params, dv[0:2], dv[2:4], dv[4:6], dv[6:8], stream=stream)
+    out = [torch.empty(t.shape, dtype=dt).pin_memory() for t in dv[6:8]]
+    for o_, t in zip(out, dv[6:8]):
+        o_.copy_(t, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    bin_ = sum(t.numel() * t.element_size() for t in pin)
+    bout = sum(t.numel() * t.element_size() for t in out)
+    return [o_.numpy() for o_ in out], rep, bin_, bout

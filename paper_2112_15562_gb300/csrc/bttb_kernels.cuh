@@ -1,0 +1,294 @@
+// Kernels of the BTTB/BCCB sensitivity products (Sec. 2.7.1).
+//
+// A 2-D transform of an Ny x Nx layer is split into a row pass (length Nx, along x)
+// and a column pass (length Ny, along y).  Real rows are transformed two at a time
+// as one complex sequence (a + i b); the half spectrum of each is recovered from
+// Z[k] and Z[N-k].  Only ncol = Nx/2 + 1 columns are kept.  Zero padding is never
+// stored: the first stage of each transform skips the inputs beyond the data.
+//
+// Forward product of one field:  rows (m -> Z) -> columns with the layer spectra
+// multiplied and summed over layers (Z -> Y) -> inverse columns (Y -> W) ->
+// inverse rows cropped to the stations (W -> d).  Adjoint: rows (r -> W) ->
+// columns (W -> Y = V^) -> per layer conj(T^_r) V^ and inverse columns (Y -> Z)
+// -> inverse rows cropped to the prisms (Z -> g).
+#pragma once
+#include "fft.cuh"
+
+namespace gj {
+
+template <typename R>
+struct OpView {
+    int sx, sy, nx, ny, nz, Nx, Ny, ncol;
+    FftPlanDev px, py;
+    const cpx<R> *twx;   // W_Nx^k, k < Nx
+    const cpx<R> *twy;   // W_Ny^k, k < Ny
+    const cpx<R> *spec;  // [nz][Ny][ncol] layer spectra / (Nx Ny)
+    cpx<R> *Z;           // [nz*ny][ncol]  row-pass output / adjoint column output
+    cpx<R> *Y;           // [Ny][ncol]     summed spectrum / residual spectrum
+    cpx<R> *W;           // [max(sy, ...)][ncol]  inverse-column output / residual rows
+};
+
+// How real lines are paired into complex transforms.
+struct PairMap {
+    int nlines;  // lines per side
+    int joint;   // 1: pair q = (line q of op0, line q of op1); 0: lines (2q, 2q+1) of op0
+    __device__ __forceinline__ int npairs() const { return joint ? nlines : (nlines + 1) >> 1; }
+    __device__ __forceinline__ void lines(int q, int &la, int &lb, bool &hasb) const {
+        if (joint) { la = q; lb = q; hasb = true; }
+        else { la = 2 * q; lb = 2 * q + 1; hasb = lb < nlines; }
+    }
+};
+
+__device__ __forceinline__ bool stopped(const int *done) {
+    return done != nullptr && *(volatile const int *)done != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, real -> half spectrum.  Pro::fetch(la, lb, hasb, j, a, b) supplies the
+// two real inputs of element j (< n_in); Pro::flush(scratch) runs once per block.
+template <typename R, class Pro>
+__global__ void __launch_bounds__(256) k_row_fwd(OpView<R> op, PairMap pm, int n_in, int P,
+                                                 cpx<R> *out0, cpx<R> *out1, Pro pro, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = op.Nx, ncol = op.ncol;
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + N * P;
+    C *tw = buf1 + N * P;
+    __shared__ double red[32];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = op.twx[i];
+    pro.init();
+    const int q0 = blockIdx.x * P;
+    const int np = pm.npairs();
+    for (int it = threadIdx.x; it < n_in * P; it += blockDim.x) {
+        const int p = it % P, j = it / P, q = q0 + p;
+        R a = 0, b = 0;
+        if (q < np) {
+            int la, lb; bool hb;
+            pm.lines(q, la, lb, hb);
+            pro.fetch(la, lb, hb, j, a, b);
+        }
+        buf0[j * P + p] = mk<C>(a, b);
+    }
+    __syncthreads();
+    C *X = fft_lines<R, false>(buf0, buf1, op.px, P, tw, n_in);
+    for (int it = threadIdx.x; it < ncol * P; it += blockDim.x) {
+        const int p = it % P, k = it / P, q = q0 + p;
+        if (q >= np) continue;
+        const C zk = X[k * P + p];
+        const C zm = X[((N - k) % N) * P + p];
+        int la, lb; bool hb;
+        pm.lines(q, la, lb, hb);
+        out0[(size_t)la * ncol + k] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (hb) out1[(size_t)lb * ncol + k] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    }
+    pro.flush(red);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass, half spectrum -> real, cropped to n_out.  Epi::store(la, lb, hasb, j, a, b).
+template <typename R, class Epi>
+__global__ void __launch_bounds__(256) k_row_inv(OpView<R> op, PairMap pm, int n_out, int P,
+                                                 const cpx<R> *in0, const cpx<R> *in1, Epi epi,
+                                                 const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = op.Nx, ncol = op.ncol;
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + N * P;
+    C *tw = buf1 + N * P;
+    __shared__ double red[32];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = op.twx[i];
+    epi.init();
+    const int q0 = blockIdx.x * P;
+    const int np = pm.npairs();
+    for (int it = threadIdx.x; it < N * P; it += blockDim.x) {
+        const int p = it % P, k = it / P, q = q0 + p;
+        C z = czero<C>();
+        if (q < np) {
+            int la, lb; bool hb;
+            pm.lines(q, la, lb, hb);
+            const bool lo = k < ncol;
+            const int kk = lo ? k : N - k;
+            C A = in0[(size_t)la * ncol + kk];
+            C B = hb ? in1[(size_t)lb * ncol + kk] : czero<C>();
+            if (kk == 0 || 2 * kk == N) { A.y = 0; B.y = 0; }
+            z = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+        }
+        buf0[k * P + p] = z;
+    }
+    __syncthreads();
+    C *X = fft_lines<R, true>(buf0, buf1, op.px, P, tw, N);
+    for (int it = threadIdx.x; it < n_out * P; it += blockDim.x) {
+        const int p = it % P, j = it / P, q = q0 + p;
+        if (q >= np) continue;
+        int la, lb; bool hb;
+        pm.lines(q, la, lb, hb);
+        const C z = X[j * P + p];
+        epi.store(la, lb, hb, j, z.x, z.y);
+    }
+    epi.flush(red);
+}
+
+// ---------------------------------------------------------------------------
+// Column pass of the forward product: for a tile of C columns and a group of
+// layers, Y += sum_r T^_r . FFT_y(Z_r).  Y must be zeroed before the launch.
+template <typename R>
+__global__ void __launch_bounds__(256) k_col_fwd_mac(OpView<R> op0, OpView<R> op1, int C, int L,
+                                                     const int *done) {
+    using Cx = cpx<R>;
+    if (stopped(done)) return;
+    const OpView<R> &op = blockIdx.z ? op1 : op0;
+    const int c0 = blockIdx.x * C;
+    const int r0 = blockIdx.y * L;
+    if (r0 >= op.nz || c0 >= op.ncol) return;
+    const int r1 = min(r0 + L, op.nz);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = op.Ny, ny = op.ny, ncol = op.ncol;
+    Cx *buf0 = reinterpret_cast<Cx *>(smem_raw);
+    Cx *buf1 = buf0 + Ny * C;
+    Cx *acc = buf1 + Ny * C;
+    Cx *tw = acc + Ny * C;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) acc[it] = czero<Cx>();
+    for (int r = r0; r < r1; ++r) {
+        const Cx *Zr = op.Z + (size_t)r * ny * ncol;
+        for (int it = threadIdx.x; it < ny * C; it += blockDim.x) {
+            const int c = it % C, iy = it / C;
+            buf0[it] = (c0 + c < ncol) ? Zr[(size_t)iy * ncol + c0 + c] : czero<Cx>();
+        }
+        __syncthreads();
+        const Cx *X = fft_lines<R, false>(buf0, buf1, op.py, C, tw, ny);
+        const Cx *Tr = op.spec + (size_t)r * Ny * ncol;
+        for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+            const int c = it % C, ky = it / C;
+            if (c0 + c < ncol) acc[it] = cadd(acc[it], cmul(X[it], Tr[(size_t)ky * ncol + c0 + c]));
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, ky = it / C;
+        if (c0 + c < ncol) {
+            R *y = reinterpret_cast<R *>(op.Y + (size_t)ky * ncol + c0 + c);
+            atomicAdd(y, acc[it].x);
+            atomicAdd(y + 1, acc[it].y);
+        }
+    }
+}
+
+// Inverse column pass of the forward product: W[jy] = IFFT_y(Y)[jy], jy < sy.
+template <typename R>
+__global__ void __launch_bounds__(256) k_col_inv(OpView<R> op0, OpView<R> op1, int C, const int *done) {
+    using Cx = cpx<R>;
+    if (stopped(done)) return;
+    const OpView<R> &op = blockIdx.y ? op1 : op0;
+    const int c0 = blockIdx.x * C;
+    if (c0 >= op.ncol) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = op.Ny, ncol = op.ncol;
+    Cx *buf0 = reinterpret_cast<Cx *>(smem_raw);
+    Cx *buf1 = buf0 + Ny * C;
+    Cx *tw = buf1 + Ny * C;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, ky = it / C;
+        buf0[it] = (c0 + c < ncol) ? op.Y[(size_t)ky * ncol + c0 + c] : czero<Cx>();
+    }
+    __syncthreads();
+    const Cx *X = fft_lines<R, true>(buf0, buf1, op.py, C, tw, Ny);
+    for (int it = threadIdx.x; it < op.sy * C; it += blockDim.x) {
+        const int c = it % C, jy = it / C;
+        if (c0 + c < ncol) op.W[(size_t)jy * ncol + c0 + c] = X[it];
+    }
+}
+
+// Forward column pass of the residual (adjoint preparation): Y = FFT_y(W), W has
+// sy nonzero rows.
+template <typename R>
+__global__ void __launch_bounds__(256) k_col_fft(OpView<R> op0, OpView<R> op1, int C, const int *done) {
+    using Cx = cpx<R>;
+    if (stopped(done)) return;
+    const OpView<R> &op = blockIdx.y ? op1 : op0;
+    const int c0 = blockIdx.x * C;
+    if (c0 >= op.ncol) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = op.Ny, ncol = op.ncol;
+    Cx *buf0 = reinterpret_cast<Cx *>(smem_raw);
+    Cx *buf1 = buf0 + Ny * C;
+    Cx *tw = buf1 + Ny * C;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
+    for (int it = threadIdx.x; it < op.sy * C; it += blockDim.x) {
+        const int c = it % C, iy = it / C;
+        buf0[it] = (c0 + c < ncol) ? op.W[(size_t)iy * ncol + c0 + c] : czero<Cx>();
+    }
+    __syncthreads();
+    const Cx *X = fft_lines<R, false>(buf0, buf1, op.py, C, tw, op.sy);
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, ky = it / C;
+        if (c0 + c < ncol) op.Y[(size_t)ky * ncol + c0 + c] = X[it];
+    }
+}
+
+// Column pass of the adjoint product: for layer r, Z_r = IFFT_y(conj(T^_r) . Y),
+// rows iy < ny.
+template <typename R>
+__global__ void __launch_bounds__(256) k_col_adj(OpView<R> op0, OpView<R> op1, int C, const int *done) {
+    using Cx = cpx<R>;
+    if (stopped(done)) return;
+    const OpView<R> &op = blockIdx.z ? op1 : op0;
+    const int c0 = blockIdx.x * C;
+    const int r = blockIdx.y;
+    if (c0 >= op.ncol || r >= op.nz) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = op.Ny, ncol = op.ncol, ny = op.ny;
+    Cx *buf0 = reinterpret_cast<Cx *>(smem_raw);
+    Cx *buf1 = buf0 + Ny * C;
+    Cx *tw = buf1 + Ny * C;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
+    const Cx *Tr = op.spec + (size_t)r * Ny * ncol;
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, ky = it / C;
+        buf0[it] = (c0 + c < ncol) ? cmulc(op.Y[(size_t)ky * ncol + c0 + c], Tr[(size_t)ky * ncol + c0 + c])
+                                   : czero<Cx>();
+    }
+    __syncthreads();
+    const Cx *X = fft_lines<R, true>(buf0, buf1, op.py, C, tw, Ny);
+    Cx *Zr = op.Z + (size_t)r * ny * ncol;
+    for (int it = threadIdx.x; it < ny * C; it += blockDim.x) {
+        const int c = it % C, iy = it / C;
+        if (c0 + c < ncol) Zr[(size_t)iy * ncol + c0 + c] = X[it];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain functors.
+
+template <typename R>
+struct LoadPlain {  // a = x0[la*pitch + j], b = x1[lb*pitch + j]
+    const R *x0;
+    const R *x1;
+    int pitch;
+    __device__ void init() {}
+    __device__ __forceinline__ void fetch(int la, int lb, bool hb, int j, R &a, R &b) const {
+        a = x0[(size_t)la * pitch + j];
+        b = hb ? x1[(size_t)lb * pitch + j] : R(0);
+    }
+    __device__ __forceinline__ void flush(double *) const {}
+};
+
+template <typename R>
+struct StorePlain {
+    R *y0;
+    R *y1;
+    int pitch;
+    __device__ void init() {}
+    __device__ __forceinline__ void store(int la, int lb, bool hb, int j, R a, R b) const {
+        y0[(size_t)la * pitch + j] = a;
+        if (hb) y1[(size_t)lb * pitch + j] = b;
+    }
+    __device__ __forceinline__ void flush(double *) const {}
+};
+
+}  // namespace gj

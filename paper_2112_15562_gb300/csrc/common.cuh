@@ -1,0 +1,63 @@
+// Shared device helpers: complex arithmetic, block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gj {
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using T = float2; };
+template <> struct CplxOf<double> { using T = double2; };
+template <typename R> using cpx = typename CplxOf<R>::T;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+    C c; c.x = a; c.y = b; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+    return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <typename C, bool INV> __device__ __forceinline__ C mul_mi(C a) {
+    return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+template <typename C> __device__ __forceinline__ C czero() { return mk<C>(0, 0); }
+
+// Sum of `v` over the block; every thread gets the result.  `scratch` holds
+// at least 32 doubles.  All threads of the block must call it.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+    if (warp == 0) {
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) scratch[0] = t;
+    }
+    __syncthreads();
+    double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+// Adds per-thread partials acc[0..K) into out[0..K) (one double atomic per
+// block per entry).  All threads must call it.
+template <int K, typename A>
+__device__ __forceinline__ void block_accumulate(const A *acc, double *out, double *scratch) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = block_sum((double)acc[k], scratch);
+        if (threadIdx.x == 0 && out) atomicAdd(out + k, s);
+    }
+}
+
+}  // namespace gj

@@ -1,0 +1,57 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gj.h"
+#include "fft.cuh"
+
+struct gj_op {
+    // geometry
+    int sx, sy, nx, ny, nz, off_x, off_y;
+    double dx, dy, station_z;
+    std::vector<double> z_edges;
+    gj_field field;
+    gj_mag mag;
+    gj_precision prec;
+    // padded sizes and plans
+    int Nx, Ny, ncol;
+    gj::FftPlanDev px, py;
+    // device memory (op precision unless noted)
+    void *twx = nullptr, *twy = nullptr;  // twiddles W_N^k
+    void *spec = nullptr;                 // [nz][Ny][ncol] complex
+    void *Z = nullptr, *Y = nullptr, *W = nullptr;
+    size_t spec_bytes = 0, ws_bytes = 0;
+    // launch shapes
+    int P_row = 8, C_col = 8, L_grp = 4;
+};
+
+namespace gj {
+
+void set_error(const std::string &msg);
+gj_status cuda_fail(cudaError_t e, const char *what);
+bool plan_size(int N, FftPlanDev &plan);   // false if N has an unsupported factor
+int  autotune_size(int minN);               // smallest 7-smooth N >= minN
+size_t elem_bytes(gj_precision p);           // bytes of one real value
+void make_twiddles(int N, std::vector<double> &re, std::vector<double> &im);
+
+// smem sizing helpers
+int pick_row_pairs(int Nx, size_t csize);
+int pick_col_tile(int Ny, size_t csize, int nbuf);
+
+template <typename R> struct OpView;
+template <typename R> OpView<R> view_of(const gj_op *op);
+
+// enqueue products (matvec.cu)
+gj_status forward_enqueue(const gj_op *op, const void *m, void *d, cudaStream_t s);
+gj_status adjoint_enqueue(const gj_op *op, const void *r, void *g, cudaStream_t s);
+
+}  // namespace gj
+
+#define GJ_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return gj::cuda_fail(_e, #call);        \
+    } while (0)

@@ -1,0 +1,92 @@
+// The Gramian coupling term (Eq. Gramian) and its ascent directions (RRCG:2-3).
+#include "view.cuh"
+
+namespace gj {
+
+// Pass 1: per-block partial sums of (m1,m1), (m2,m2), (m1,m2).  Products and the
+// per-thread sums use the vector precision; block and grid sums use FP64.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gram_dots(int64_t n, const R *m1, const R *m2, double *part) {
+    __shared__ double red[32];
+    R a11 = 0, a22 = 0, a12 = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R x = m1[i], y = m2[i];
+        a11 += x * x; a22 += y * y; a12 += x * y;
+    }
+    const double s11 = block_sum((double)a11, red);
+    const double s22 = block_sum((double)a22, red);
+    const double s12 = block_sum((double)a12, red);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = s11;
+        part[3 * blockIdx.x + 1] = s22;
+        part[3 * blockIdx.x + 2] = s12;
+    }
+}
+
+// Pass 2 (one block): fixed-order sum of the partials into sums[0..3).
+__global__ void k_gram_finish(int nb, const double *part, double *sums) {
+    __shared__ double red[32];
+    for (int c = 0; c < 3; ++c) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[3 * b + c];
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) sums[c] = t;
+    }
+}
+
+// Pass 3: ascent directions and ||m2 - (a12/a11) m1||^2 partials, which give
+// S = a11 ||m2 - (a12/a11) m1||^2 without the cancellation of a11 a22 - a12^2.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gram_dirs(int64_t n, const R *m1, const R *m2, const double *sums,
+                                                   R *l1, R *l2, double *part) {
+    __shared__ double red[32];
+    const double a11 = sums[0], a22 = sums[1], a12 = sums[2];
+    const R c11 = (R)a11, c22 = (R)a22, c12 = (R)a12;
+    const R ratio = a11 > 0 ? (R)(a12 / a11) : R(0);
+    R res = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R x = m1[i], y = m2[i];
+        if (l1) l1[i] = c22 * x - c12 * y;
+        if (l2) l2[i] = c11 * y - c12 * x;
+        const R d = y - ratio * x;
+        res += d * d;
+    }
+    const double s = block_sum((double)res, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_gram_value(int nb, const double *part, const double *sums, double *S) {
+    __shared__ double red[32];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[b];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) *S = sums[0] > 0 ? sums[0] * t : 0.0;
+}
+
+template <typename R>
+static gj_status gramian_launch(int64_t n, const void *m1, const void *m2, double *S, void *l1, void *l2,
+                                cudaStream_t st) {
+    const int nb = (int)std::min<int64_t>(4 * 152, std::max<int64_t>(1, (n + 255) / 256));
+    double *scratch = nullptr;
+    GJ_CUDA(cudaMallocAsync(&scratch, (3 * nb + 3) * sizeof(double), st));
+    double *part = scratch, *sums = scratch + 3 * nb;
+    k_gram_dots<R><<<nb, 256, 0, st>>>(n, (const R *)m1, (const R *)m2, part);
+    k_gram_finish<<<1, 256, 0, st>>>(nb, part, sums);
+    k_gram_dirs<R><<<nb, 256, 0, st>>>(n, (const R *)m1, (const R *)m2, sums, (R *)l1, (R *)l2, part);
+    k_gram_value<<<1, 256, 0, st>>>(nb, part, sums, S);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gramian launch");
+    return GJ_OK;
+}
+
+}  // namespace gj
+
+extern "C" gj_status gj_gramian_value_grad(int64_t n, gj_precision prec, const void *m1, const void *m2,
+                                           double *S, void *l1, void *l2, gj_stream_t stream) {
+    if (n < 1 || !m1 || !m2 || !S) { gj::set_error("gj_gramian_value_grad: bad argument"); return GJ_ERR_ARG; }
+    if (prec != GJ_FP64 && prec != GJ_FP32_MIXED) { gj::set_error("gj_gramian_value_grad: bad precision"); return GJ_ERR_ARG; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return prec == GJ_FP64 ? gj::gramian_launch<double>(n, m1, m2, S, l1, l2, st)
+                           : gj::gramian_launch<float>(n, m1, m2, S, l1, l2, st);
+}

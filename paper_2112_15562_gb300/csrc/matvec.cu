@@ -1,0 +1,88 @@
+// G m and G^T r of one field (Sec. 2.7.1): the C-ABI entry points and the launch
+// sequences shared with the solver.
+#include "view.cuh"
+
+namespace gj {
+
+template <typename R>
+static void launch_forward(const gj_op *o, const R *m, R *d, cudaStream_t st) {
+    OpView<R> v = view_of<R>(o);
+    const size_t cs = sizeof(cpx<R>);
+    // rows: m -> Z (pairs of consecutive (layer, row) lines)
+    PairMap pm{o->nz * o->ny, 0};
+    const int P = o->P_row;
+    const size_t rsm = row_smem(o->Nx, P, cs);
+    cudaFuncSetAttribute(k_row_fwd<R, LoadPlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    const int npr = (pm.nlines + 1) / 2;
+    k_row_fwd<R, LoadPlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
+                                                                    LoadPlain<R>{m, m, o->nx}, nullptr);
+    // columns with the layer spectra, summed over layers
+    cudaMemsetAsync(v.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
+    const int C = o->C_col;
+    const int nt = (o->ncol + C - 1) / C;
+    const size_t msm = col_smem(o->Ny, C, 3, cs);
+    cudaFuncSetAttribute(k_col_fwd_mac<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+    k_col_fwd_mac<R><<<dim3(nt, (o->nz + o->L_grp - 1) / o->L_grp, 1), 256, msm, st>>>(v, v, C, o->L_grp, nullptr);
+    // inverse columns
+    const size_t ism = col_smem(o->Ny, C, 2, cs);
+    cudaFuncSetAttribute(k_col_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    k_col_inv<R><<<dim3(nt, 1), 256, ism, st>>>(v, v, C, nullptr);
+    // inverse rows, cropped to the stations
+    PairMap ps{o->sy, 0};
+    const int nps = (ps.nlines + 1) / 2;
+    cudaFuncSetAttribute(k_row_inv<R, StorePlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    k_row_inv<R, StorePlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
+                                                                     StorePlain<R>{d, d, o->sx}, nullptr);
+}
+
+template <typename R>
+static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
+    OpView<R> v = view_of<R>(o);
+    const size_t cs = sizeof(cpx<R>);
+    const int P = o->P_row;
+    const size_t rsm = row_smem(o->Nx, P, cs);
+    // rows of the residual -> W
+    PairMap ps{o->sy, 0};
+    const int nps = (ps.nlines + 1) / 2;
+    cudaFuncSetAttribute(k_row_fwd<R, LoadPlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    k_row_fwd<R, LoadPlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
+                                                                    LoadPlain<R>{r, r, o->sx}, nullptr);
+    const int C = o->C_col;
+    const int nt = (o->ncol + C - 1) / C;
+    const size_t sm2 = col_smem(o->Ny, C, 2, cs);
+    cudaFuncSetAttribute(k_col_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    k_col_fft<R><<<dim3(nt, 1), 256, sm2, st>>>(v, v, C, nullptr);
+    cudaFuncSetAttribute(k_col_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    k_col_adj<R><<<dim3(nt, o->nz, 1), 256, sm2, st>>>(v, v, C, nullptr);
+    PairMap pm{o->nz * o->ny, 0};
+    const int npr = (pm.nlines + 1) / 2;
+    cudaFuncSetAttribute(k_row_inv<R, StorePlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    k_row_inv<R, StorePlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
+                                                                     StorePlain<R>{g, g, o->nx}, nullptr);
+}
+
+gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {
+    if (o->prec == GJ_FP64) launch_forward<double>(o, (const double *)m, (double *)d, st);
+    else launch_forward<float>(o, (const float *)m, (float *)d, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GJ_OK : cuda_fail(e, "g_forward launch");
+}
+
+gj_status adjoint_enqueue(const gj_op *o, const void *r, void *g, cudaStream_t st) {
+    if (o->prec == GJ_FP64) launch_adjoint<double>(o, (const double *)r, (double *)g, st);
+    else launch_adjoint<float>(o, (const float *)r, (float *)g, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GJ_OK : cuda_fail(e, "g_adjoint launch");
+}
+
+}  // namespace gj
+
+extern "C" gj_status gj_g_forward(const gj_op *op, const void *m, void *d, gj_stream_t stream) {
+    if (!op || !m || !d) { gj::set_error("gj_g_forward: NULL argument"); return GJ_ERR_ARG; }
+    return gj::forward_enqueue(op, m, d, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gj_status gj_g_adjoint(const gj_op *op, const void *r, void *g, gj_stream_t stream) {
+    if (!op || !r || !g) { gj::set_error("gj_g_adjoint: NULL argument"); return GJ_ERR_ARG; }
+    return gj::adjoint_enqueue(op, r, g, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,699 @@
+// Regularised reweighted CG joint solve (Eq. RRCG:1-8) with Lp reweighting
+// (Eq. W, Eq. WL), the Gramian coupling in the original space (RRCG:2-3),
+// bounds (Sec. 2.5), the chi^2 stop (Eq. chi2) and the alpha schedule
+// (Eq. regpara).  All vector work is fused into the prologues and epilogues of
+// the FFT row passes; the scalars stay on the device.
+//
+// One loop body (iteration k -> k+1), both fields in every launch:
+//   adjoint:  rows of v = W_d r~ -> columns -> conj-spectrum columns -> rows with
+//             l = W^-1 A^T v + alpha (W m - W m_apr) + lambda l_G      (RRCG:4)
+//   forward:  rows of p = l + beta p_prev, x = W^-1 p -> columns -> rows with
+//             ||A~ p||^2                                              (RRCG:5-6)
+//   scalars:  s = (p, l) / (||A~p||^2 + (alpha + lambda)||p||^2)
+//   forward:  rows with m <- clip(m - s W^-1 p) and the Gramian sums -> columns
+//             -> rows with r~ = W_d (A m - d), Phi = ||r~||^2          (RRCG:7-8, 1)
+//   scalars:  chi^2 flags, alpha freeze/decay, stop flag
+// The first forward of m_0 and its scalars run once when the solver is created.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "view.cuh"
+
+namespace gj {
+
+struct SolverDev {
+    int k, done, status, pending_update;
+    int sat[2];
+    int kmax, stop_on_chi2, per_field;
+    int p[2];
+    double eps2;
+    double alpha[2], q[2], alpha_min[2], lam[2], lo[2], hi[2];
+    double chi2_target[2];
+    double s[2], beta[2];
+    double ll_prev[2];
+    double phi_last[2], SG_last;
+    // accumulators, zeroed after use
+    double G[3];          // (m1,m1), (m2,m2), (m1,m2) of the current models
+    double phi[2];        // ||r~||^2
+    double ll[2];         // ||l||^2
+    double pl[2], pp[2];  // (p,l), ||p||^2
+    double qq[2];         // ||A~ p||^2
+    gj_rrcg_hist *hist;
+};
+
+template <typename R>
+struct FieldVecs {
+    R *m[2];
+    R *p[2];
+    R *l[2];
+    R *v[2];               // W_d r~ (s values)
+    const R *wd[2];        // 1 / sigma
+    const R *dobs[2];
+    const R *mapr[2];      // may be null
+    const R *wdep[2];      // nz values
+    const R *whard[2];     // may be null
+};
+
+template <typename R> __device__ __forceinline__ R rsqrt_t(R x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// Diagonal of W = W_depth W_hard W_L at cell c of layer r (Eq. W, Eq. WL).
+template <typename R>
+__device__ __forceinline__ R weight(const FieldVecs<R> &F, int i, int p, R eps2, int r, size_t c, R m) {
+    R w = F.wdep[i][r];
+    if (F.whard[i]) w *= F.whard[i][c];
+    if (p == 1) {
+        const R d = m - (F.mapr[i] ? F.mapr[i][c] : R(0));
+        w *= rsqrt_t<R>(sqrt(d * d + eps2));
+    }
+    return w;
+}
+
+// Forward of m with the pending model update (RRCG:7-8 and the bounds) and the
+// Gramian sums of the updated models.
+template <typename R>
+struct ProModel {
+    FieldVecs<R> F;
+    SolverDev *S;
+    int nx, ny;
+    // per-thread
+    int upd, pw[2];
+    R s[2], lo[2], hi[2], eps2;
+    R acc[3];
+    __device__ void init() {
+        upd = S->pending_update;
+        eps2 = (R)S->eps2;
+        for (int i = 0; i < 2; ++i) {
+            s[i] = (R)S->s[i]; lo[i] = (R)S->lo[i]; hi[i] = (R)S->hi[i]; pw[i] = S->p[i];
+        }
+        acc[0] = acc[1] = acc[2] = 0;
+    }
+    __device__ __forceinline__ void fetch(int la, int lb, bool, int j, R &a, R &b) {
+        const size_t c = (size_t)la * nx + j;
+        const int r = la / ny;
+        R mv[2];
+        for (int i = 0; i < 2; ++i) {
+            R mi = F.m[i][c];
+            if (upd) {
+                const R w = weight(F, i, pw[i], eps2, r, c, mi);
+                mi = mi - s[i] * F.p[i][c] / w;
+                mi = fmin(fmax(mi, lo[i]), hi[i]);
+                F.m[i][c] = mi;
+            }
+            mv[i] = mi;
+        }
+        acc[0] += mv[0] * mv[0];
+        acc[1] += mv[1] * mv[1];
+        acc[2] += mv[0] * mv[1];
+        a = mv[0];
+        b = mv[1];
+    }
+    __device__ void flush(double *red) { block_accumulate<3>(acc, S->G, red); }
+};
+
+// Residual epilogue: r~ = W_d (A m - d), v = W_d r~, Phi partials (RRCG:1).
+template <typename R>
+struct EpiResidual {
+    FieldVecs<R> F;
+    SolverDev *S;
+    int sx;
+    R acc[2];
+    __device__ void init() { acc[0] = acc[1] = 0; }
+    __device__ __forceinline__ void store(int la, int, bool, int j, R a, R b) {
+        const size_t t = (size_t)la * sx + j;
+        const R y[2] = {a, b};
+        for (int i = 0; i < 2; ++i) {
+            const R w = F.wd[i][t];
+            const R rt = w * (y[i] - F.dobs[i][t]);
+            acc[i] += rt * rt;
+            F.v[i][t] = w * rt;
+        }
+    }
+    __device__ void flush(double *red) { block_accumulate<2>(acc, S->phi, red); }
+};
+
+template <typename R>
+struct LoadPair {
+    const R *x0;
+    const R *x1;
+    int pitch;
+    __device__ void init() {}
+    __device__ __forceinline__ void fetch(int la, int lb, bool, int j, R &a, R &b) const {
+        a = x0[(size_t)la * pitch + j];
+        b = x1[(size_t)lb * pitch + j];
+    }
+    __device__ void flush(double *) {}
+};
+
+// Gradient epilogue (RRCG:2-4): l = W^-1 A^T v + alpha (W m - W m_apr) + lambda l_G.
+template <typename R>
+struct EpiGradient {
+    FieldVecs<R> F;
+    SolverDev *S;
+    int nx, ny;
+    R alpha[2], lam[2], eps2, g11, g22, g12;
+    int pw[2];
+    R acc[2];
+    __device__ void init() {
+        for (int i = 0; i < 2; ++i) { alpha[i] = (R)S->alpha[i]; lam[i] = (R)S->lam[i]; pw[i] = S->p[i]; }
+        eps2 = (R)S->eps2;
+        g11 = (R)S->G[0]; g22 = (R)S->G[1]; g12 = (R)S->G[2];
+        acc[0] = acc[1] = 0;
+    }
+    __device__ __forceinline__ void store(int la, int, bool, int j, R a, R b) {
+        const size_t c = (size_t)la * nx + j;
+        const int r = la / ny;
+        const R m1 = F.m[0][c], m2 = F.m[1][c];
+        const R lG[2] = {g22 * m1 - g12 * m2, g11 * m2 - g12 * m1};
+        const R g[2] = {a, b};
+        const R mm[2] = {m1, m2};
+        for (int i = 0; i < 2; ++i) {
+            const R w = weight(F, i, pw[i], eps2, r, c, mm[i]);
+            const R ma = F.mapr[i] ? F.mapr[i][c] : R(0);
+            const R li = g[i] / w + alpha[i] * (w * mm[i] - w * ma) + lam[i] * lG[i];
+            F.l[i][c] = li;
+            acc[i] += li * li;
+        }
+    }
+    __device__ void flush(double *red) { block_accumulate<2>(acc, S->ll, red); }
+};
+
+// Search direction (RRCG:5) and the forward input W^-1 p.
+template <typename R>
+struct ProDirection {
+    FieldVecs<R> F;
+    SolverDev *S;
+    int nx, ny;
+    R beta[2], eps2;
+    int first, pw[2];
+    R acc[4];  // (p,l)_0, (p,l)_1, ||p||^2_0, ||p||^2_1
+    __device__ void init() {
+        first = S->k == 0;
+        eps2 = (R)S->eps2;
+        for (int i = 0; i < 2; ++i) pw[i] = S->p[i];
+        if (S->per_field) {
+            for (int i = 0; i < 2; ++i) beta[i] = S->ll_prev[i] > 0 ? (R)(S->ll[i] / S->ll_prev[i]) : R(0);
+        } else {
+            const double den = S->ll_prev[0] + S->ll_prev[1];
+            const R b = den > 0 ? (R)((S->ll[0] + S->ll[1]) / den) : R(0);
+            beta[0] = beta[1] = b;
+        }
+        acc[0] = acc[1] = acc[2] = acc[3] = 0;
+    }
+    __device__ __forceinline__ void fetch(int la, int, bool, int j, R &a, R &b) {
+        const size_t c = (size_t)la * nx + j;
+        const int r = la / ny;
+        R x[2];
+        for (int i = 0; i < 2; ++i) {
+            const R li = F.l[i][c];
+            const R pi = first ? li : li + beta[i] * F.p[i][c];
+            F.p[i][c] = pi;
+            acc[i] += pi * li;
+            acc[2 + i] += pi * pi;
+            x[i] = pi / weight(F, i, pw[i], eps2, r, c, F.m[i][c]);
+        }
+        a = x[0];
+        b = x[1];
+    }
+    __device__ void flush(double *red) {
+        block_accumulate<2>(acc, S->pl, red);
+        block_accumulate<2>(acc + 2, S->pp, red);
+    }
+};
+
+// ||A~ p||^2 = ||W_d A (W^-1 p)||^2 partials (RRCG:6).
+template <typename R>
+struct EpiQNorm {
+    FieldVecs<R> F;
+    SolverDev *S;
+    int sx;
+    R acc[2];
+    __device__ void init() { acc[0] = acc[1] = 0; }
+    __device__ __forceinline__ void store(int la, int, bool, int j, R a, R b) {
+        const size_t t = (size_t)la * sx + j;
+        const R q0 = F.wd[0][t] * a, q1 = F.wd[1][t] * b;
+        acc[0] += q0 * q0;
+        acc[1] += q1 * q1;
+    }
+    __device__ void flush(double *red) { block_accumulate<2>(acc, S->qq, red); }
+};
+
+// chi^2 test, alpha schedule and stop (Eq. chi2, Eq. regpara); one thread.
+__global__ void k_scalars_after_residual(SolverDev *S) {
+    if (S->done) return;
+    const int k = S->k;
+    for (int i = 0; i < 2; ++i)
+        if (S->phi[i] <= S->chi2_target[i]) S->sat[i] = 1;
+    if (k > 0)
+        for (int i = 0; i < 2; ++i)
+            if (!S->sat[i]) S->alpha[i] = fmax(S->q[i] * S->alpha[i], S->alpha_min[i]);
+    const double SG = S->G[0] * S->G[1] - S->G[2] * S->G[2];
+    S->phi_last[0] = S->phi[0];
+    S->phi_last[1] = S->phi[1];
+    S->SG_last = SG;
+    if (S->hist) {
+        gj_rrcg_hist &h = S->hist[k];
+        h.phi[0] = S->phi[0]; h.phi[1] = S->phi[1];
+        h.alpha[0] = S->alpha[0]; h.alpha[1] = S->alpha[1];
+        h.S_G = SG;
+        h.s[0] = h.s[1] = h.beta[0] = h.beta[1] = 0.0;
+    }
+    S->pending_update = 0;
+    if (!isfinite(S->phi[0]) || !isfinite(S->phi[1])) {
+        S->status = GJ_ERR_NONFINITE;
+        S->done = 1;
+        return;
+    }
+    if ((S->stop_on_chi2 && S->sat[0] && S->sat[1]) || k >= S->kmax) S->done = 1;
+    S->phi[0] = S->phi[1] = 0.0;
+}
+
+// Step length s_k (RRCG:6); one thread.
+__global__ void k_scalars_after_direction(SolverDev *S) {
+    if (S->done) return;
+    const int k = S->k;
+    double den[2], beta[2];
+    for (int i = 0; i < 2; ++i) den[i] = S->qq[i] + (S->alpha[i] + S->lam[i]) * S->pp[i];
+    if (S->per_field) {
+        for (int i = 0; i < 2; ++i) {
+            S->s[i] = den[i] > 0 ? S->pl[i] / den[i] : 0.0;
+            beta[i] = (k > 0 && S->ll_prev[i] > 0) ? S->ll[i] / S->ll_prev[i] : 0.0;
+        }
+    } else {
+        const double d = den[0] + den[1];
+        const double s = d > 0 ? (S->pl[0] + S->pl[1]) / d : 0.0;
+        S->s[0] = S->s[1] = s;
+        const double lp = S->ll_prev[0] + S->ll_prev[1];
+        beta[0] = beta[1] = (k > 0 && lp > 0) ? (S->ll[0] + S->ll[1]) / lp : 0.0;
+    }
+    if (S->hist) {
+        gj_rrcg_hist &h = S->hist[k];
+        h.s[0] = S->s[0]; h.s[1] = S->s[1];
+        h.beta[0] = beta[0]; h.beta[1] = beta[1];
+    }
+    if (!isfinite(S->s[0]) || !isfinite(S->s[1])) {
+        S->status = GJ_ERR_NONFINITE;
+        S->done = 1;
+        return;
+    }
+    S->ll_prev[0] = S->ll[0];
+    S->ll_prev[1] = S->ll[1];
+    S->ll[0] = S->ll[1] = 0.0;
+    S->pl[0] = S->pl[1] = S->pp[0] = S->pp[1] = 0.0;
+    S->qq[0] = S->qq[1] = 0.0;
+    S->G[0] = S->G[1] = S->G[2] = 0.0;
+    S->pending_update = 1;
+    S->k = k + 1;
+}
+
+template <typename R>
+__global__ void k_reciprocal(int n, const R *sigma, R *wd) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wd[i] = R(1) / sigma[i];
+}
+
+}  // namespace gj
+
+using namespace gj;
+
+struct ProfilePair { cudaEvent_t a, b; };
+
+struct gj_rrcg {
+    const gj_op *op[2];
+    gj_precision prec;
+    SolverDev *S = nullptr;   // device
+    void *buf = nullptr;      // p, l (2 fields each, n), v (2 x s), wd (2 x s)
+    const void *dobs[2], *mapr[2], *wdep[2], *whard[2];
+    void *m[2];
+    gj_rrcg_hist *hist = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int profile = 0;
+    std::vector<ProfilePair> eager_pairs;   // recorded since the last read
+    std::vector<ProfilePair> graph_pairs;   // owned by the captured graph
+    std::vector<ProfilePair> free_pairs;
+    bool capturing = false;
+};
+
+namespace gj {
+
+static ProfilePair take_pair(gj_rrcg *sv) {
+    ProfilePair p;
+    if (!sv->free_pairs.empty()) { p = sv->free_pairs.back(); sv->free_pairs.pop_back(); }
+    else { cudaEventCreate(&p.a); cudaEventCreate(&p.b); }
+    return p;
+}
+
+template <typename R>
+struct SolverLaunch {
+    gj_rrcg *sv;
+    OpView<R> v0, v1;
+    FieldVecs<R> F;
+    int P, C, L;
+    size_t rsm, msm, csm;
+    int n_rows_cells, n_rows_st;  // pairs in the cell / station row passes
+
+    void setup() {  // views and launch shapes only (no CUDA calls: safe during capture)
+        const gj_op *o = sv->op[0];
+        v0 = view_of<R>(sv->op[0]);
+        v1 = view_of<R>(sv->op[1]);
+        const size_t cs = sizeof(cpx<R>);
+        P = o->P_row; C = o->C_col; L = o->L_grp;
+        rsm = row_smem(o->Nx, P, cs);
+        msm = col_smem(o->Ny, C, 3, cs);
+        csm = col_smem(o->Ny, C, 2, cs);
+        const int n = o->nx * o->ny * o->nz, s = o->sx * o->sy;
+        R *b = static_cast<R *>(sv->buf);
+        for (int i = 0; i < 2; ++i) {
+            F.m[i] = static_cast<R *>(sv->m[i]);
+            F.p[i] = b + (size_t)i * n;
+            F.l[i] = b + (size_t)(2 + i) * n;
+            F.v[i] = b + (size_t)4 * n + (size_t)i * s;
+            F.wd[i] = b + (size_t)4 * n + (size_t)(2 + i) * s;
+            F.dobs[i] = static_cast<const R *>(sv->dobs[i]);
+            F.mapr[i] = static_cast<const R *>(sv->mapr[i]);
+            F.wdep[i] = static_cast<const R *>(sv->wdep[i]);
+            F.whard[i] = static_cast<const R *>(sv->whard[i]);
+        }
+    }
+
+    void set_attributes() {
+        cudaFuncSetAttribute(k_row_fwd<R, ProModel<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_row_fwd<R, ProDirection<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_row_fwd<R, LoadPair<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_row_inv<R, EpiResidual<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_row_inv<R, EpiGradient<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_row_inv<R, EpiQNorm<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        cudaFuncSetAttribute(k_col_fwd_mac<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+        cudaFuncSetAttribute(k_col_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        cudaFuncSetAttribute(k_col_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        cudaFuncSetAttribute(k_col_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    }
+
+    // Forward columns (Y = sum_r T^_r FFT_y(Z_r)) and inverse columns, both fields.
+    void forward_columns(cudaStream_t st) {
+        const gj_op *o = sv->op[0];
+        const size_t cs = sizeof(cpx<R>);
+        cudaMemsetAsync(v0.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
+        cudaMemsetAsync(v1.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
+        const int nt = (o->ncol + C - 1) / C;
+        ProfilePair pp{};
+        if (sv->profile) {
+            pp = take_pair(sv);
+            cudaEventRecord(pp.a, st);
+        }
+        k_col_fwd_mac<R><<<dim3(nt, (o->nz + L - 1) / L, 2), 256, msm, st>>>(v0, v1, C, L, &sv->S->done);
+        if (sv->profile) {
+            cudaEventRecord(pp.b, st);
+            (sv->capturing ? sv->graph_pairs : sv->eager_pairs).push_back(pp);
+        }
+        k_col_inv<R><<<dim3(nt, 2), 256, csm, st>>>(v0, v1, C, &sv->S->done);
+    }
+
+    void head(cudaStream_t st) {  // forward of (updated) m, residual, chi^2 scalars
+        const gj_op *o = sv->op[0];
+        const int *done = &sv->S->done;
+        PairMap pc{o->nz * o->ny, 1};
+        ProModel<R> pm{F, sv->S, o->nx, o->ny};
+        k_row_fwd<R, ProModel<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pm, done);
+        forward_columns(st);
+        PairMap ps{o->sy, 1};
+        EpiResidual<R> er{F, sv->S, o->sx};
+        k_row_inv<R, EpiResidual<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, er, done);
+        k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
+    }
+
+    void body(cudaStream_t st) {
+        const gj_op *o = sv->op[0];
+        const int *done = &sv->S->done;
+        const int nt = (o->ncol + C - 1) / C;
+        PairMap ps{o->sy, 1};
+        PairMap pc{o->nz * o->ny, 1};
+        // adjoint: rows of v -> W, columns -> Y, per-layer conj-spectrum columns -> Z
+        LoadPair<R> lv{F.v[0], F.v[1], o->sx};
+        k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, lv, done);
+        k_col_fft<R><<<dim3(nt, 2), 256, csm, st>>>(v0, v1, C, done);
+        k_col_adj<R><<<dim3(nt, o->nz, 2), 256, csm, st>>>(v0, v1, C, done);
+        EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
+        k_row_inv<R, EpiGradient<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, eg, done);
+        // direction and its forward product
+        ProDirection<R> pd{F, sv->S, o->nx, o->ny};
+        k_row_fwd<R, ProDirection<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pd, done);
+        forward_columns(st);
+        EpiQNorm<R> eq{F, sv->S, o->sx};
+        k_row_inv<R, EpiQNorm<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, eq, done);
+        k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
+        // model update, its forward product and the chi^2 scalars
+        head(st);
+    }
+};
+
+template <typename R>
+static void run_head(gj_rrcg *sv, cudaStream_t st) {
+    SolverLaunch<R> L{sv};
+    L.setup();
+    L.set_attributes();
+    L.head(st);
+}
+
+template <typename R>
+static void run_body(gj_rrcg *sv, cudaStream_t st) {
+    SolverLaunch<R> L{sv};
+    L.setup();
+    L.body(st);
+}
+
+static gj_status check_ops(const gj_op *const ops[2]) {
+    if (!ops || !ops[0] || !ops[1]) { set_error("rrcg: ops must be non-NULL"); return GJ_ERR_ARG; }
+    const gj_op *a = ops[0], *b = ops[1];
+    if (a->field != GJ_GRAVITY || b->field != GJ_MAGNETIC) {
+        set_error("rrcg: ops[0] must be gravity and ops[1] magnetic"); return GJ_ERR_ARG;
+    }
+    if (a->sx != b->sx || a->sy != b->sy || a->nx != b->nx || a->ny != b->ny || a->nz != b->nz ||
+        a->Nx != b->Nx || a->Ny != b->Ny || a->prec != b->prec) {
+        set_error("rrcg: both operators must share grid sizes, padded sizes and precision"); return GJ_ERR_ARG;
+    }
+    return GJ_OK;
+}
+
+}  // namespace gj
+
+extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_params *P,
+                                    const void *const dobs[2], const void *const sigma[2],
+                                    const void *const m_apr[2], const void *const w_depth[2],
+                                    const void *const w_hard[2], void *const m[2], gj_rrcg_hist *hist,
+                                    gj_stream_t stream, gj_rrcg **out) {
+    if (!out) { set_error("gj_rrcg_create: out is NULL"); return GJ_ERR_ARG; }
+    *out = nullptr;
+    gj_status rc = check_ops(ops);
+    if (rc != GJ_OK) return rc;
+    if (!P || !dobs || !sigma || !w_depth || !m) { set_error("gj_rrcg_create: NULL argument"); return GJ_ERR_ARG; }
+    for (int i = 0; i < 2; ++i) {
+        if (!dobs[i] || !sigma[i] || !w_depth[i] || !m[i]) { set_error("gj_rrcg_create: NULL vector"); return GJ_ERR_ARG; }
+        if (P->p[i] != 1 && P->p[i] != 2) { set_error("gj_rrcg_create: p must be 1 or 2"); return GJ_ERR_ARG; }
+        if (!(P->lo[i] <= P->hi[i])) { set_error("gj_rrcg_create: lo must not exceed hi"); return GJ_ERR_ARG; }
+        if (!(P->alpha1[i] >= 0) || !(P->lambda[i] >= 0) || !(P->q[i] > 0)) {
+            set_error("gj_rrcg_create: alpha1, lambda must be >= 0 and q > 0"); return GJ_ERR_ARG;
+        }
+    }
+    if (P->kmax < 0) { set_error("gj_rrcg_create: kmax must be >= 0"); return GJ_ERR_ARG; }
+    if (!(P->eps2 > 0)) { set_error("gj_rrcg_create: eps2 must be > 0"); return GJ_ERR_ARG; }
+    if (P->scalars < 0 || P->scalars > 2) { set_error("gj_rrcg_create: bad scalars mode"); return GJ_ERR_ARG; }
+    gj_rrcg *sv = new (std::nothrow) gj_rrcg();
+    if (!sv) { set_error("gj_rrcg_create: host allocation failed"); return GJ_ERR_OOM; }
+    const gj_op *o = ops[0];
+    sv->op[0] = ops[0]; sv->op[1] = ops[1];
+    sv->prec = o->prec;
+    for (int i = 0; i < 2; ++i) {
+        sv->dobs[i] = dobs[i];
+        sv->mapr[i] = m_apr ? m_apr[i] : nullptr;
+        sv->wdep[i] = w_depth[i];
+        sv->whard[i] = w_hard ? w_hard[i] : nullptr;
+        sv->m[i] = m[i];
+    }
+    sv->hist = hist;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t es = elem_bytes(o->prec);
+    const size_t n = (size_t)o->nx * o->ny * o->nz, s = (size_t)o->sx * o->sy;
+    cudaError_t e;
+    if ((e = cudaMalloc(&sv->S, sizeof(SolverDev))) != cudaSuccess) { delete sv; return cuda_fail(e, "solver state"); }
+    if ((e = cudaMalloc(&sv->buf, (4 * n + 4 * s) * es)) != cudaSuccess) {
+        cudaFree(sv->S); delete sv; return cuda_fail(e, "solver vectors");
+    }
+    SolverDev h{};
+    h.kmax = P->kmax;
+    h.stop_on_chi2 = P->stop_on_chi2;
+    const bool lam0 = P->lambda[0] == 0 && P->lambda[1] == 0;
+    h.per_field = P->scalars == GJ_SCALARS_PER_FIELD || (P->scalars == GJ_SCALARS_AUTO && lam0);
+    h.eps2 = P->eps2;
+    for (int i = 0; i < 2; ++i) {
+        h.p[i] = P->p[i];
+        h.alpha[i] = P->alpha1[i]; h.q[i] = P->q[i]; h.alpha_min[i] = P->alpha_min[i];
+        h.lam[i] = P->lambda[i]; h.lo[i] = P->lo[i]; h.hi[i] = P->hi[i];
+        h.chi2_target[i] = (double)s + sqrt(2.0 * (double)s);
+    }
+    h.hist = hist;
+    cudaMemcpyAsync(sv->S, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(sv->buf, 0, 4 * n * es, st);
+    // W_d = 1 / sigma
+    for (int i = 0; i < 2; ++i) {
+        void *wd = static_cast<char *>(sv->buf) + (4 * n + (2 + i) * s) * es;
+        if (o->prec == GJ_FP64)
+            k_reciprocal<double><<<64, 256, 0, st>>>((int)s, (const double *)sigma[i], (double *)wd);
+        else
+            k_reciprocal<float><<<64, 256, 0, st>>>((int)s, (const float *)sigma[i], (float *)wd);
+    }
+    if (o->prec == GJ_FP64) run_head<double>(sv, st); else run_head<float>(sv, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(sv->S); cudaFree(sv->buf); delete sv;
+        return cuda_fail(e, "gj_rrcg_create");
+    }
+    *out = sv;
+    return GJ_OK;
+}
+
+extern "C" gj_status gj_rrcg_iterate(gj_rrcg *sv, int iters, int use_graph, gj_stream_t stream) {
+    if (!sv || iters < 0) { set_error("gj_rrcg_iterate: bad argument"); return GJ_ERR_ARG; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (use_graph) {
+        if (!sv->exec) {
+            if (sv->profile)
+                for (int i = 0; i < 4; ++i) {
+                    ProfilePair p;
+                    GJ_CUDA(cudaEventCreate(&p.a));
+                    GJ_CUDA(cudaEventCreate(&p.b));
+                    sv->free_pairs.push_back(p);
+                }
+            cudaStream_t cap;
+            GJ_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            sv->capturing = true;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                if (sv->prec == GJ_FP64) run_body<double>(sv, cap); else run_body<float>(sv, cap);
+                e = cudaStreamEndCapture(cap, &sv->graph);
+            }
+            sv->capturing = false;
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return cuda_fail(e, "rrcg graph capture");
+            GJ_CUDA(cudaGraphInstantiate(&sv->exec, sv->graph, 0));
+        }
+        for (int it = 0; it < iters; ++it) GJ_CUDA(cudaGraphLaunch(sv->exec, st));
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            if (sv->prec == GJ_FP64) run_body<double>(sv, st); else run_body<float>(sv, st);
+        }
+        GJ_CUDA(cudaGetLastError());
+    }
+    return GJ_OK;
+}
+
+extern "C" gj_status gj_rrcg_report_get(gj_rrcg *sv, gj_rrcg_report *rep, gj_stream_t stream) {
+    if (!sv || !rep) { set_error("gj_rrcg_report_get: NULL argument"); return GJ_ERR_ARG; }
+    SolverDev h;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GJ_CUDA(cudaMemcpyAsync(&h, sv->S, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GJ_CUDA(cudaStreamSynchronize(st));
+    rep->status = h.status;
+    rep->iterations = h.k;
+    rep->converged = h.sat[0] && h.sat[1];
+    rep->satisfied[0] = h.sat[0];
+    rep->satisfied[1] = h.sat[1];
+    rep->phi[0] = h.phi_last[0];
+    rep->phi[1] = h.phi_last[1];
+    rep->alpha[0] = h.alpha[0];
+    rep->alpha[1] = h.alpha[1];
+    rep->S_G = h.SG_last;
+    return GJ_OK;
+}
+
+extern "C" int gj_rrcg_done(gj_rrcg *sv, gj_stream_t stream) {
+    if (!sv) return -1;
+    int d = 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&d, &sv->S->done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    return d;
+}
+
+extern "C" gj_status gj_rrcg_profile(gj_rrcg *sv, int enable) {
+    if (!sv) { set_error("gj_rrcg_profile: NULL solver"); return GJ_ERR_ARG; }
+    if (enable && sv->exec && sv->graph_pairs.empty()) {
+        // the graph was captured without events: capture again
+        cudaGraphExecDestroy(sv->exec); sv->exec = nullptr;
+        cudaGraphDestroy(sv->graph); sv->graph = nullptr;
+    }
+    sv->profile = enable ? 1 : 0;
+    return GJ_OK;
+}
+
+extern "C" gj_status gj_rrcg_profile_read(gj_rrcg *sv, int *launches, double *total_ms) {
+    if (!sv || !launches || !total_ms) { set_error("gj_rrcg_profile_read: NULL argument"); return GJ_ERR_ARG; }
+    GJ_CUDA(cudaDeviceSynchronize());
+    double tot = 0.0;
+    int cnt = 0;
+    auto acc = [&](const std::vector<ProfilePair> &v) -> gj_status {
+        for (const auto &p : v) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, p.a, p.b);
+            if (e != cudaSuccess) return cuda_fail(e, "gj_rrcg_profile_read");
+            tot += ms;
+            ++cnt;
+        }
+        return GJ_OK;
+    };
+    gj_status rc = acc(sv->eager_pairs);
+    if (rc != GJ_OK) return rc;
+    if (sv->exec) { rc = acc(sv->graph_pairs); if (rc != GJ_OK) return rc; }
+    for (auto &p : sv->eager_pairs) sv->free_pairs.push_back(p);
+    sv->eager_pairs.clear();
+    *launches = cnt;
+    *total_ms = tot;
+    return GJ_OK;
+}
+
+extern "C" void gj_rrcg_destroy(gj_rrcg *sv) {
+    if (!sv) return;
+    cudaDeviceSynchronize();
+    if (sv->exec) cudaGraphExecDestroy(sv->exec);
+    if (sv->graph) cudaGraphDestroy(sv->graph);
+    for (auto *v : {&sv->eager_pairs, &sv->graph_pairs, &sv->free_pairs})
+        for (auto &p : *v) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    cudaFree(sv->S);
+    cudaFree(sv->buf);
+    delete sv;
+}
+
+extern "C" gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrcg_params *P,
+                                         const void *const dobs[2], const void *const sigma[2],
+                                         const void *const m_apr[2], const void *const w_depth[2],
+                                         const void *const w_hard[2], void *const m[2], gj_rrcg_hist *hist,
+                                         gj_rrcg_report *rep, gj_stream_t stream) {
+    if (!rep) { set_error("gj_rrcg_joint_solve: rep is NULL"); return GJ_ERR_ARG; }
+    gj_rrcg *sv = nullptr;
+    gj_status rc = gj_rrcg_create(ops, P, dobs, sigma, m_apr, w_depth, w_hard, m, hist, stream, &sv);
+    if (rc != GJ_OK) return rc;
+    int left = P->kmax;
+    const int chunk = 8;
+    while (left > 0) {
+        const int it = std::min(chunk, left);
+        rc = gj_rrcg_iterate(sv, it, 1, stream);
+        if (rc != GJ_OK) break;
+        left -= it;
+        const int d = gj_rrcg_done(sv, stream);
+        if (d < 0) { rc = cuda_fail(cudaGetLastError(), "gj_rrcg_joint_solve"); break; }
+        if (d) break;
+    }
+    if (rc == GJ_OK) rc = gj_rrcg_report_get(sv, rep, stream);
+    gj_rrcg_destroy(sv);
+    if (rc == GJ_OK && rep->status != GJ_OK) {
+        set_error("gj_rrcg_joint_solve: non-finite scalar");
+        return (gj_status)rep->status;
+    }
+    return rc;
+}

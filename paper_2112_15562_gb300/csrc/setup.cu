@@ -1,0 +1,393 @@
+// Operator setup (Sec. 2.7.1): prism kernel tables of every depth layer, their
+// BCCB embedding and 2-D spectra.  All geometry arithmetic runs in FP64.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "view.cuh"
+
+namespace gj {
+
+// ---------------------------------------------------------------------------
+// Closed-form prism fields as corner sums of antiderivatives (Sec. 2.1 cites
+// Haaz for the vertical gravity and Rao & Babu for the total-field anomaly).
+// u = x' - x0, v = y' - y0, w = z' - z0 (z down) with w >= 0 at every corner;
+// u and v are never zero because corners sit half a cell from the stations.
+
+// ln(a + R) for R = sqrt(a^2 + b^2 + c^2); for a < 0 use (b^2 + c^2) / (R - a).
+__device__ __forceinline__ double log_a_plus_r(double a, double R, double b, double c) {
+    return a >= 0.0 ? log(a + R) : log((b * b + c * c) / (R - a));
+}
+
+// Antiderivative whose mixed third derivative is w / R^3.
+__device__ __forceinline__ double gravity_corner(double u, double v, double w) {
+    const double R = sqrt(u * u + v * v + w * w);
+    return -(u * log_a_plus_r(v, R, u, w) + v * log_a_plus_r(u, R, v, w) - w * atan2(u * v, w * R));
+}
+
+// t^T H t with H the antiderivatives of the second derivatives of 1/R, weights
+// c = (txx, tyy, tzz, 2txy, 2txz, 2tyz).
+struct MagCoef { double c[6]; };
+
+__device__ __forceinline__ double magnetic_corner(double u, double v, double w, const MagCoef &k) {
+    const double R = sqrt(u * u + v * v + w * w);
+    const double hxx = -atan(v * w / (u * R));
+    const double hyy = -atan(u * w / (v * R));
+    const double hzz = -atan2(u * v, w * R);
+    const double hxy = log_a_plus_r(w, R, u, v);
+    const double hxz = log_a_plus_r(v, R, u, w);
+    const double hyz = log_a_plus_r(u, R, v, w);
+    return k.c[0] * hxx + k.c[1] * hyy + k.c[2] * hzz + k.c[3] * hxy + k.c[4] * hxz + k.c[5] * hyz;
+}
+
+struct Lattice {
+    int nbx1, nby1, nz1;     // lattice points in u, v, w
+    int a_max, b_max;
+    double dx, dy;
+    const double *zw;        // nz + 1 values of w
+};
+
+__global__ void k_corner_lattice(Lattice L, int magnetic, MagCoef mc, double *out) {
+    const size_t total = (size_t)L.nbx1 * L.nby1 * L.nz1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % L.nbx1);
+        const int f = (int)((i / L.nbx1) % L.nby1);
+        const int k = (int)(i / ((size_t)L.nbx1 * L.nby1));
+        const double u = (-(double)L.b_max - 0.5 + e) * L.dx;
+        const double v = (-(double)L.a_max - 0.5 + f) * L.dy;
+        const double w = L.zw[k];
+        out[i] = magnetic ? magnetic_corner(u, v, w, mc) : gravity_corner(u, v, w);
+    }
+}
+
+// Row-pass input of the setup: the circulant embedding of layer r's table,
+// T[c_y mod Ny][c_x mod Nx] = K(c_y + off_y, c_x + off_x) for c in
+// [-(n-1), s-1], zero elsewhere; K is the 8-corner sum of the lattice.
+struct LoadTable {
+    const double *lat;
+    int nbx1, nby1;
+    int Nx, Ny, sx, sy, nx, ny, off_x, off_y, a_max, b_max;
+    double scale;
+    __device__ void init() {}
+    __device__ double value(int line, int j) const {
+        const int r = line / Ny, iy = line % Ny;
+        int cy, cx;
+        if (iy <= sy - 1) cy = iy; else if (iy >= Ny - (ny - 1)) cy = iy - Ny; else return 0.0;
+        if (j <= sx - 1) cx = j; else if (j >= Nx - (nx - 1)) cx = j - Nx; else return 0.0;
+        const int e = b_max - (cx + off_x);
+        const int f = a_max - (cy + off_y);
+        double s = 0.0;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int df = 0; df < 2; ++df)
+#pragma unroll
+                for (int de = 0; de < 2; ++de) {
+                    const double t = lat[((size_t)(r + dk) * nby1 + (f + df)) * nbx1 + (e + de)];
+                    s += ((de + df + dk) & 1) ? t : -t;
+                }
+        return s * scale;
+    }
+    __device__ __forceinline__ void fetch(int la, int lb, bool hb, int j, double &a, double &b) const {
+        a = value(la, j);
+        b = hb ? value(lb, j) : 0.0;
+    }
+    __device__ __forceinline__ void flush(double *) const {}
+};
+
+// Column pass of the setup: spec[r] = FFT_y of the row-pass output of layer r.
+template <typename Rout>
+__global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const double2 *Zs, cpx<Rout> *spec, int C) {
+    using Cx = double2;
+    const int c0 = blockIdx.x * C;
+    const int r = blockIdx.y;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = op.Ny, ncol = op.ncol;
+    Cx *buf0 = reinterpret_cast<Cx *>(smem_raw);
+    Cx *buf1 = buf0 + Ny * C;
+    Cx *tw = buf1 + Ny * C;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
+    const Cx *Zr = Zs + (size_t)r * Ny * ncol;
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, iy = it / C;
+        buf0[it] = (c0 + c < ncol) ? Zr[(size_t)iy * ncol + c0 + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const Cx *X = fft_lines<double, false>(buf0, buf1, op.py, C, tw, Ny);
+    cpx<Rout> *Sr = spec + (size_t)r * Ny * ncol;
+    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
+        const int c = it % C, ky = it / C;
+        if (c0 + c < ncol) Sr[(size_t)ky * ncol + c0 + c] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+
+bool plan_size(int N, FftPlanDev &plan) {
+    if (N < 1 || N > 4096) return false;
+    int n = N, e = 0;
+    while (n % 2 == 0) { n /= 2; ++e; }
+    std::vector<int> rs(e / 3, 8);
+    if (e % 3 == 1) {
+        if (!rs.empty()) { rs.back() = 4; rs.push_back(4); } else rs.push_back(2);
+    } else if (e % 3 == 2) {
+        rs.push_back(4);
+    }
+    const int primes[] = {3, 5, 7, 11, 13, 17};
+    for (int p : primes)
+        while (n % p == 0) { n /= p; rs.push_back(p); }
+    if (n != 1) return false;
+    if ((int)rs.size() > kMaxStages) return false;
+    plan.N = N;
+    plan.nst = (int)rs.size();
+    for (int i = 0; i < kMaxStages; ++i) plan.radix[i] = i < plan.nst ? rs[i] : 1;
+    return true;
+}
+
+int autotune_size(int minN) {
+    for (int N = std::max(1, minN);; ++N) {
+        int n = N;
+        for (int p : {2, 3, 5, 7})
+            while (n % p == 0) n /= p;
+        if (n == 1) return N;
+    }
+}
+
+void make_twiddles(int N, std::vector<double> &re, std::vector<double> &im) {
+    re.resize(N);
+    im.resize(N);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < N; ++k) {
+        // exact values at the quarter points keep the small radices exact
+        if (4 * k % N == 0) {
+            const int q = 4 * k / N;
+            const double c[4] = {1, 0, -1, 0}, s[4] = {0, -1, 0, 1};
+            re[k] = c[q];
+            im[k] = s[q];
+        } else {
+            const double a = two_pi * (double)k / (double)N;
+            re[k] = std::cos(a);
+            im[k] = -std::sin(a);
+        }
+    }
+}
+
+size_t elem_bytes(gj_precision p) { return p == GJ_FP64 ? sizeof(double) : sizeof(float); }
+
+int pick_row_pairs(int Nx, size_t cs) {
+    int P = 16;
+    while (P > 1 && row_smem(Nx, P, cs) > 96 * 1024) P >>= 1;
+    return P;
+}
+
+int pick_col_tile(int Ny, size_t cs, int nbuf) {
+    int C = 16;
+    while (C > 1 && col_smem(Ny, C, nbuf, cs) > 100 * 1024) C >>= 1;
+    return C;
+}
+
+static gj_status upload_twiddles(int N, gj_precision prec, void **out) {
+    std::vector<double> re, im;
+    make_twiddles(N, re, im);
+    if (prec == GJ_FP64) {
+        std::vector<double2> h(N);
+        for (int k = 0; k < N; ++k) h[k] = make_double2(re[k], im[k]);
+        GJ_CUDA(cudaMalloc(out, N * sizeof(double2)));
+        GJ_CUDA(cudaMemcpy(*out, h.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float2> h(N);
+        for (int k = 0; k < N; ++k) h[k] = make_float2((float)re[k], (float)im[k]);
+        GJ_CUDA(cudaMalloc(out, N * sizeof(float2)));
+        GJ_CUDA(cudaMemcpy(*out, h.data(), N * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    return GJ_OK;
+}
+
+static void free_op_memory(gj_op *op) {
+    if (!op) return;
+    cudaFree(op->twx); cudaFree(op->twy); cudaFree(op->spec);
+    cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W);
+    op->twx = op->twy = op->spec = op->Z = op->Y = op->W = nullptr;
+}
+
+template <typename Rout>
+static gj_status build_spectra(gj_op *op, cudaStream_t st) {
+    // FP64 twiddles for the setup transforms
+    void *twx64 = nullptr, *twy64 = nullptr;
+    double *lat = nullptr;
+    double2 *Zs = nullptr;
+    gj_status rc = GJ_OK;
+    auto cleanup = [&]() {
+        cudaFree(lat); cudaFree(Zs);
+        if (op->prec != GJ_FP64) { cudaFree(twx64); cudaFree(twy64); }
+    };
+    if (op->prec == GJ_FP64) {
+        twx64 = op->twx;
+        twy64 = op->twy;
+    } else {
+        if ((rc = upload_twiddles(op->Nx, GJ_FP64, &twx64)) != GJ_OK) { cleanup(); return rc; }
+        if ((rc = upload_twiddles(op->Ny, GJ_FP64, &twy64)) != GJ_OK) { cleanup(); return rc; }
+    }
+    Lattice L;
+    L.b_max = op->off_x + op->sx - 1;
+    L.a_max = op->off_y + op->sy - 1;
+    L.nbx1 = op->sx + op->nx;
+    L.nby1 = op->sy + op->ny;
+    L.nz1 = op->nz + 1;
+    L.dx = op->dx;
+    L.dy = op->dy;
+    std::vector<double> zw(op->nz + 1);
+    for (int k = 0; k <= op->nz; ++k) zw[k] = op->z_edges[k] - op->station_z;
+    double *zw_d = nullptr;
+    const size_t nlat = (size_t)L.nbx1 * L.nby1 * L.nz1;
+    cudaError_t e;
+    if ((e = cudaMalloc(&lat, nlat * sizeof(double))) != cudaSuccess) { cleanup(); return cuda_fail(e, "lattice"); }
+    if ((e = cudaMalloc(&Zs, (size_t)op->nz * op->Ny * op->ncol * sizeof(double2))) != cudaSuccess) {
+        cleanup(); return cuda_fail(e, "setup rows");
+    }
+    if ((e = cudaMalloc(&zw_d, zw.size() * sizeof(double))) != cudaSuccess) { cleanup(); return cuda_fail(e, "zw"); }
+    cudaMemcpy(zw_d, zw.data(), zw.size() * sizeof(double), cudaMemcpyHostToDevice);
+    L.zw = zw_d;
+
+    MagCoef mc{};
+    double scale = 1.0 / ((double)op->Nx * (double)op->Ny);
+    const int magnetic = op->field == GJ_MAGNETIC;
+    if (magnetic) {
+        const double d2r = 3.14159265358979323846 / 180.0;
+        const double I = op->mag.incl_deg * d2r, D = op->mag.decl_deg * d2r;
+        const double t[3] = {std::cos(I) * std::sin(D), std::cos(I) * std::cos(D), std::sin(I)};
+        mc.c[0] = t[0] * t[0]; mc.c[1] = t[1] * t[1]; mc.c[2] = t[2] * t[2];
+        mc.c[3] = 2 * t[0] * t[1]; mc.c[4] = 2 * t[0] * t[2]; mc.c[5] = 2 * t[1] * t[2];
+        scale *= op->mag.F_nT / (4.0 * 3.14159265358979323846);
+    } else {
+        // G = 6.6743e-11 m^3 kg^-1 s^-2; g/cc -> kg/m^3 (1e3); m/s^2 -> mGal (1e5)
+        scale *= 6.6743e-11 * 1.0e3 * 1.0e5;
+    }
+    k_corner_lattice<<<1216, 256, 0, st>>>(L, magnetic, mc, lat);
+
+    OpView<double> v{};
+    v.sx = op->sx; v.sy = op->sy; v.nx = op->nx; v.ny = op->ny; v.nz = op->nz;
+    v.Nx = op->Nx; v.Ny = op->Ny; v.ncol = op->ncol; v.px = op->px; v.py = op->py;
+    v.twx = static_cast<const double2 *>(twx64);
+    v.twy = static_cast<const double2 *>(twy64);
+
+    LoadTable lt;
+    lt.lat = lat; lt.nbx1 = L.nbx1; lt.nby1 = L.nby1;
+    lt.Nx = op->Nx; lt.Ny = op->Ny; lt.sx = op->sx; lt.sy = op->sy; lt.nx = op->nx; lt.ny = op->ny;
+    lt.off_x = op->off_x; lt.off_y = op->off_y; lt.a_max = L.a_max; lt.b_max = L.b_max;
+    lt.scale = scale;
+    PairMap pm{op->nz * op->Ny, 0};
+    const int P = pick_row_pairs(op->Nx, sizeof(double2));
+    const int npairs = (pm.nlines + 1) / 2;
+    const size_t rsm = row_smem(op->Nx, P, sizeof(double2));
+    cudaFuncSetAttribute(k_row_fwd<double, LoadTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    k_row_fwd<double, LoadTable><<<(npairs + P - 1) / P, 256, rsm, st>>>(v, pm, op->Nx, P, Zs, Zs, lt, nullptr);
+    const int C = pick_col_tile(op->Ny, sizeof(double2), 2);
+    const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
+    cudaFuncSetAttribute(k_col_spec<Rout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    dim3 g((op->ncol + C - 1) / C, op->nz);
+    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(zw_d);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "spectra setup");
+    return GJ_OK;
+}
+
+}  // namespace gj
+
+using namespace gj;
+
+extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag, gj_precision prec,
+                                   int Npad_y, int Npad_x, gj_stream_t stream, gj_op **out) {
+    if (!out) { set_error("gj_bttb_setup: out is NULL"); return GJ_ERR_ARG; }
+    *out = nullptr;
+    if (!grid) { set_error("gj_bttb_setup: grid is NULL"); return GJ_ERR_ARG; }
+    const gj_grid &G = *grid;
+    if (G.sx < 1 || G.sy < 1 || G.nx < 1 || G.ny < 1 || G.nz < 1) {
+        set_error("gj_bttb_setup: sizes must be >= 1"); return GJ_ERR_ARG;
+    }
+    if (!(G.dx > 0) || !(G.dy > 0) || !G.z_edges) {
+        set_error("gj_bttb_setup: dx, dy must be > 0 and z_edges set"); return GJ_ERR_ARG;
+    }
+    for (int k = 0; k < G.nz; ++k)
+        if (!(G.z_edges[k + 1] > G.z_edges[k])) { set_error("gj_bttb_setup: z_edges must increase"); return GJ_ERR_ARG; }
+    if (!(G.station_z <= G.z_edges[0])) {
+        set_error("gj_bttb_setup: stations must lie at or above the top of the mesh"); return GJ_ERR_ARG;
+    }
+    if (field != GJ_GRAVITY && field != GJ_MAGNETIC) { set_error("gj_bttb_setup: bad field"); return GJ_ERR_ARG; }
+    if (field == GJ_MAGNETIC && !mag) { set_error("gj_bttb_setup: magnetic field needs gj_mag"); return GJ_ERR_ARG; }
+    if (prec != GJ_FP64 && prec != GJ_FP32_MIXED) { set_error("gj_bttb_setup: bad precision"); return GJ_ERR_ARG; }
+    const int minx = G.sx + G.nx - 1, miny = G.sy + G.ny - 1;
+    int Nx = Npad_x > 0 ? Npad_x : autotune_size(minx);
+    int Ny = Npad_y > 0 ? Npad_y : autotune_size(miny);
+    if (Nx < minx || Ny < miny) {
+        set_error("gj_bttb_setup: padded size must be >= stations + prisms - 1 in each direction");
+        return GJ_ERR_ARG;
+    }
+    gj_op *op = new (std::nothrow) gj_op();
+    if (!op) { set_error("gj_bttb_setup: host allocation failed"); return GJ_ERR_OOM; }
+    if (!plan_size(Nx, op->px) || !plan_size(Ny, op->py)) {
+        delete op;
+        set_error("gj_bttb_setup: padded size unsupported (must be <= 4096 with prime factors <= 17)");
+        return GJ_ERR_UNSUPPORTED;
+    }
+    op->sx = G.sx; op->sy = G.sy; op->nx = G.nx; op->ny = G.ny; op->nz = G.nz;
+    op->off_x = G.off_x; op->off_y = G.off_y; op->dx = G.dx; op->dy = G.dy; op->station_z = G.station_z;
+    op->z_edges.assign(G.z_edges, G.z_edges + G.nz + 1);
+    op->field = field;
+    op->mag = mag ? *mag : gj_mag{0, 0, 0};
+    op->prec = prec;
+    op->Nx = Nx; op->Ny = Ny; op->ncol = Nx / 2 + 1;
+    const size_t cs = 2 * elem_bytes(prec);
+    op->P_row = pick_row_pairs(Nx, cs);
+    op->C_col = pick_col_tile(Ny, cs, 3);
+    op->L_grp = 4;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gj_status rc;
+    cudaError_t e;
+    if ((rc = upload_twiddles(Nx, prec, &op->twx)) != GJ_OK) goto fail;
+    if ((rc = upload_twiddles(Ny, prec, &op->twy)) != GJ_OK) goto fail;
+    op->spec_bytes = (size_t)G.nz * Ny * op->ncol * cs;
+    if ((e = cudaMalloc(&op->spec, op->spec_bytes)) != cudaSuccess) { rc = cuda_fail(e, "spectra"); goto fail; }
+    rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
+    if (rc != GJ_OK) goto fail;
+    {
+        const size_t zb = (size_t)G.nz * G.ny * op->ncol * cs;
+        const size_t yb = (size_t)Ny * op->ncol * cs;
+        const size_t wb = (size_t)std::max(G.sy, 1) * op->ncol * cs;
+        op->ws_bytes = zb + yb + wb;
+        if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMalloc(&op->Y, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+    }
+    *out = op;
+    return GJ_OK;
+fail:
+    free_op_memory(op);
+    delete op;
+    return rc;
+}
+
+extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {
+    if (!op || !info) { set_error("gj_op_info: NULL argument"); return GJ_ERR_ARG; }
+    info->sx = op->sx; info->sy = op->sy; info->nx = op->nx; info->ny = op->ny; info->nz = op->nz;
+    info->Nx = op->Nx; info->Ny = op->Ny; info->ncol = op->ncol;
+    info->field = op->field; info->precision = op->prec;
+    info->spectrum_bytes = (int64_t)op->spec_bytes;
+    info->workspace_bytes = (int64_t)op->ws_bytes;
+    return GJ_OK;
+}
+
+extern "C" void gj_op_destroy(gj_op *op) {
+    if (!op) return;
+    cudaDeviceSynchronize();
+    free_op_memory(op);
+    delete op;
+}

@@ -1,0 +1,128 @@
+"""Parity of the CUDA BTTB/FFT products (gj_g_forward, gj_g_adjoint; Sec. 2.7.1)
+with the FP64 dense oracle (Eq. d=gm), through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import operator as oop
+from tests.gpu_common import TOL, lib, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MAG = synth.Mag(50000.0, 60.0, 10.0)
+
+
+def _grid(sx, sy, nx, ny, nz, dx=50.0, dy=None, dz=None, off=(0, 0), station_z=0.0, zvar=False):
+    g = synth.uniform_grid(sx, sy, nx, ny, nz, dx, dz=dz, off_x=off[0], off_y=off[1], station_z=station_z)
+    if dy is not None:
+        g.dy = dy
+    if zvar:
+        g.z_edges = np.concatenate([[0.0], np.cumsum(np.linspace(20.0, 80.0, nz))])
+    return g
+
+
+CASES = {
+    "joint16": (_grid(16, 16, 16, 16, 8), (0, 0)),
+    "ragged": (_grid(13, 11, 13, 11, 5, dx=30.0), (0, 0)),
+    "padding_prisms": (_grid(9, 7, 12, 10, 3, dx=40.0, dy=55.0, dz=30.0, off=(2, 1)), (0, 0)),
+    "radix_3_5_17": (_grid(8, 8, 8, 8, 3), (15, 17)),
+    "radix_11_13": (_grid(8, 8, 8, 8, 2), (22, 26)),
+    "radix_7_odd": (_grid(10, 9, 10, 9, 2), (21, 49)),
+    "lifted_varz": (_grid(12, 12, 12, 12, 6, station_z=-15.0, zvar=True), (0, 0)),
+    "one_cell": (_grid(1, 1, 1, 1, 1), (0, 0)),
+    "one_row": (_grid(7, 1, 7, 1, 4), (0, 0)),
+    "column": (_grid(1, 6, 1, 6, 2), (0, 0)),
+}
+
+
+@pytest.fixture(scope="module")
+def gj():
+    return lib()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("field", ["gravity", "magnetic"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_products_match_dense_oracle(gj, case, field, prec):
+    g, npad = CASES[case]
+    f = oop.GRAVITY if field == "gravity" else oop.MAGNETIC
+    A = oop.dense_matrix(g, f, MAG)
+    op = gj.bttb_setup(g, field, MAG if field == "magnetic" else None, precision=prec, npad=npad)
+    rng = np.random.default_rng(11)
+    for trial in range(2):
+        m = rng.uniform(0.0, 1.0, g.n) if trial == 0 else rng.standard_normal(g.n)
+        r = rng.standard_normal(g.s)
+        d = op.forward(to_dev(m, prec)).cpu().numpy()
+        a = op.adjoint(to_dev(r, prec)).cpu().numpy()
+        assert rel(d, A @ m) <= TOL[prec], (case, field, prec, rel(d, A @ m))
+        assert rel(a, A.T @ r) <= TOL[prec], (case, field, prec, rel(a, A.T @ r))
+    op.close()
+
+
+def test_padded_size_does_not_change_the_product(gj):
+    g = _grid(8, 8, 8, 8, 3)
+    A = oop.dense_matrix(g, oop.MAGNETIC, MAG)
+    m = np.random.default_rng(2).standard_normal(g.n)
+    for npad in [(15, 15), (16, 16), (18, 20), (24, 27), (30, 25), (32, 64)]:
+        op = gj.bttb_setup(g, "magnetic", MAG, precision="fp64", npad=npad)
+        assert op.info.Ny == npad[0] and op.info.Nx == npad[1]
+        assert rel(op.forward(to_dev(m, "fp64")).cpu().numpy(), A @ m) <= 1e-10
+
+
+def test_invalid_arguments_raise(gj):
+    g = _grid(8, 8, 8, 8, 3)
+    with pytest.raises(gj.GJError):
+        gj.bttb_setup(g, "gravity", npad=(14, 15))  # below s + n - 1
+    with pytest.raises(gj.GJError):
+        gj.bttb_setup(g, "gravity", npad=(19 * 1, 19))  # prime factor 19
+    with pytest.raises(gj.GJError):
+        gj.bttb_setup(g, "magnetic", None)
+    bad = _grid(8, 8, 8, 8, 3, station_z=10.0)
+    with pytest.raises(gj.GJError):
+        gj.bttb_setup(bad, "gravity")
+
+
+@pytest.fixture(scope="module")
+def c2_tables():
+    w = synth.operator_128()
+    return w, {oop.GRAVITY: oop.kernel_table(w.grid, oop.GRAVITY), oop.MAGNETIC: oop.kernel_table(w.grid, oop.MAGNETIC, w.mag)}
+
+
+@pytest.mark.parametrize("npad", [(255, 255), (0, 0)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_operator_128_sampled_rows(gj, c2_tables, npad, prec):
+    """128x128 stations, 128x128x32 cells; padded 255x255 (3*5*17) and the autotuned size."""
+    w, K = c2_tables
+    g = w.grid
+    rng = np.random.default_rng(5)
+    st = np.unique(np.concatenate([[0, g.s - 1, g.sx - 1, g.s - g.sx], rng.integers(0, g.s, 40)]))
+    cells = np.unique(np.concatenate([[0, g.n - 1], rng.integers(0, g.n, 40)]))
+    r = rng.standard_normal(g.s)
+    for f, name in [(oop.GRAVITY, "gravity"), (oop.MAGNETIC, "magnetic")]:
+        op = gj.bttb_setup(g, name, w.mag if name == "magnetic" else None, precision=prec, npad=npad)
+        m = w.m_true[0] if f == oop.GRAVITY else w.m_true[1]
+        d = op.forward(to_dev(m, prec)).cpu().numpy()
+        a = op.adjoint(to_dev(r, prec)).cpu().numpy()
+        d_ref = oop.forward_rows(K[f], g, m, st)
+        a_ref = oop.adjoint_cols(K[f], g, r, cells)
+        scale_d = np.abs(d_ref).max()
+        scale_a = np.abs(a_ref).max()
+        tol = 1e-10 if prec == "fp64" else 2e-5
+        assert np.abs(d[st] - d_ref).max() <= tol * scale_d, (name, np.abs(d[st] - d_ref).max() / scale_d)
+        assert np.abs(a[cells] - a_ref).max() <= tol * scale_a, (name, np.abs(a[cells] - a_ref).max() / scale_a)
+        op.close()
+
+
+def test_operator_128_adjoint_identity_fp64(gj, c2_tables):
+    w, _ = c2_tables
+    g = w.grid
+    rng = np.random.default_rng(8)
+    for name in ("gravity", "magnetic"):
+        op = gj.bttb_setup(g, name, w.mag if name == "magnetic" else None, precision="fp64")
+        m = rng.standard_normal(g.n)
+        r = rng.standard_normal(g.s)
+        d = op.forward(to_dev(m, "fp64")).cpu().numpy()
+        a = op.adjoint(to_dev(r, "fp64")).cpu().numpy()
+        lhs, rhs = d @ r, m @ a
+        assert abs(lhs - rhs) <= 1e-12 * np.sqrt((d @ d) * (r @ r)), (name, lhs, rhs)
+        op.close()

@@ -1,0 +1,128 @@
+"""Parity of the CUDA joint RRCG solve (gj_rrcg_joint_solve, Eq. RRCG:1-8,
+Secs. 2.5, 2.6, 2.8) with the FP64 oracle, iteration by iteration."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import operator as oop
+from oracle import weights as owt
+from oracle.rrcg import RRCGParams, rrcg_joint
+from tests.gpu_common import lib, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def joint_case(w):
+    g = w.grid
+    A = [oop.dense_matrix(g, oop.GRAVITY), oop.dense_matrix(g, oop.MAGNETIC, w.mag)]
+    d_ex = [A[i] @ w.m_true[i] for i in range(2)]
+    obs = [owt.noisy_data(d_ex[i], *w.tau[i], w.noise[i]) for i in range(2)]
+    dob = [o[0] for o in obs]
+    sig = [o[1] for o in obs]
+    wdep = [owt.depth_weights(g.z_edges, 2.0), owt.depth_weights(g.z_edges, 3.0)]
+    return g, A, dob, sig, wdep
+
+
+def run_oracle(g, A, dob, sig, wdep, P, m0=None):
+    m0 = [np.zeros(g.n)] * 2 if m0 is None else m0
+    return rrcg_joint([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
+                      dob, sig, m0, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)], P)
+
+
+def run_gpu(gj, w, g, dob, sig, wdep, prec, kw, m0=None, graph=None):
+    ops = [gj.bttb_setup(g, "gravity", precision=prec), gj.bttb_setup(g, "magnetic", w.mag, precision=prec)]
+    m = [to_dev(np.zeros(g.n) if m0 is None else m0[i], prec) for i in range(2)]
+    args = ([to_dev(x, prec) for x in dob], [to_dev(x, prec) for x in sig], [to_dev(x, prec) for x in wdep], m)
+    P = gj.solver_params(**kw)
+    if graph is None:
+        rep = gj.rrcg_joint_solve(ops, P, *args, history=True)
+    else:
+        sv = gj.Solver(ops, P, *args, history=True)
+        left = kw["kmax"]
+        while left > 0 and not sv.done():
+            sv.iterate(min(5, left), use_graph=graph)
+            left -= 5
+        rep = sv.report()
+        sv.close()
+    return [t.cpu().numpy().astype(np.float64) for t in m], rep
+
+
+KW = dict(p=(1, 1), alpha1=(2e4, 2e4), q=(0.95, 0.95), lam=(50.0, 1500.0), lo=(0.0, 0.0), hi=(1.0, 0.1),
+          kmax=50, stop_on_chi2=False)
+
+
+def oracle_params(kw):
+    return RRCGParams(p=kw["p"], alpha1=kw["alpha1"], q=kw["q"], alpha_min=kw.get("alpha_min", (0.0, 0.0)),
+                      lam=kw["lam"], lo=kw["lo"], hi=kw["hi"], kmax=kw["kmax"], stop_on_chi2=kw["stop_on_chi2"],
+                      scalars=kw.get("scalars", "auto"))
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = synth.small_joint()
+    return (w,) + joint_case(w)
+
+
+def compare_history(hg, ho, tol):
+    assert len(hg) == len(ho)
+    for k, (a, b) in enumerate(zip(hg, ho)):
+        for i in range(2):
+            assert a["phi"][i] == pytest.approx(b["phi"][i], rel=tol), (k, "phi", i)
+            assert a["alpha"][i] == pytest.approx(b["alpha"][i], rel=1e-14), (k, "alpha", i)
+            if "s" in b:
+                assert a["s"][i] == pytest.approx(b["s"][i], rel=tol), (k, "s", i)
+                assert a["beta"][i] == pytest.approx(b["beta"][i], rel=tol, abs=1e-300), (k, "beta", i)
+
+
+def test_joint_fp64_matches_oracle_step_by_step(small):
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(KW))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp64", KW)
+    assert rep["iterations"] == ref.iterations == 50
+    compare_history(rep["history"], ref.history, 1e-9)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-9
+        assert m[i].min() >= KW["lo"][i] and m[i].max() <= KW["hi"][i]
+
+
+def test_joint_fp32_mixed_within_model_tolerance(small):
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(KW))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", KW)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
+
+
+@pytest.mark.parametrize("variant", ["per_field_lam0", "p2_joint", "alpha_floor_stop"])
+def test_solver_variants_fp64(small, variant):
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    kw = dict(KW)
+    if variant == "per_field_lam0":
+        kw.update(lam=(0.0, 0.0), kmax=30)
+    elif variant == "p2_joint":
+        kw.update(p=(2, 2), lam=(50.0, 8e5), alpha1=(2e4, 4e4), alpha_min=(50.0, 50.0), kmax=40)
+    else:
+        kw.update(alpha_min=(500.0, 900.0), q=(0.8, 0.85), kmax=150, stop_on_chi2=True)
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp64", kw)
+    assert rep["iterations"] == ref.iterations
+    assert rep["converged"] == ref.converged
+    compare_history(rep["history"], ref.history, 1e-8)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-8
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_stepwise_graph_and_eager_match_one_shot(small, graph):
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    kw = dict(KW, kmax=12)
+    m1, r1 = run_gpu(gj, w, g, dob, sig, wdep, "fp64", kw)
+    m2, r2 = run_gpu(gj, w, g, dob, sig, wdep, "fp64", kw, graph=graph)
+    assert r1["iterations"] == r2["iterations"] == 12
+    for i in range(2):
+        assert rel(m2[i], m1[i]) <= 1e-12
