@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the joint gravity-magnetic RRCG hot path on one or more GB300s.
+
+Workload: 256x256 stations over 256x256x40 prisms of 100 m (2.6 M cells per model),
+gravity and magnetic fields, Lp (p = 1) stabilisers and the Gramian coupling
+(lambda = 2, 100), FP32 vectors and FFTs with FP64 scalars, padded BCCB size
+512x512.  One step = one RRCG iteration (2 forward and 1 adjoint BTTB product per
+field plus every fused vector update), replayed as one CUDA graph.  Inputs are
+seeded and synthetic (three dipping blocks, 1 % noise).  The L2 cache is flushed
+(256 MB write) before every timed step; each step is timed with CUDA events.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (a
+bounded sample of the same workload, extrapolated to one iteration).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RRCG iters/s (joint gravity+magnetic, 256^2x40, FP32 vectors+FFTs, FP64 scalars)"
+UNIT = "iters/s"
+CONFIG = {"workload": "joint RRCG 256x256 stations x 256x256x40 prisms (100 m), p=1, lambda=(2,100), Npad 512x512",
+          "cells_per_model": 256 * 256 * 40, "stations": 256 * 256, "fields": 2,
+          "l2": "flushed before each timed step (256 MB write)", "inputs": "seeded synthetic (3 dipping blocks, 1% noise)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64, operator, e2e and CPU legs")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample
+
+def oracle_sample(grid_full, mag, rows: int, cols: int, layers: int = 4, seed: int = 0):
+    """Times the oracle's direct sums on a sample and extrapolates to one RRCG
+    iteration (2 forward products and 1 adjoint product per field).  Forward rows
+    are timed on the top ``layers`` layers and scaled by nz / layers (the cost of
+    a row is linear in the layer count); adjoint cells are independent of nz."""
+    import numpy as np
+    import synth
+    from oracle import operator as oop
+
+    g = grid_full
+    sub = synth.uniform_grid(g.sx, g.sy, g.nx, g.ny, layers, g.dx)
+    sub.z_edges = g.z_edges[:layers + 1].copy()
+    rng = np.random.default_rng(seed)
+    t_rows = t_cols = 0.0
+    for f in (oop.GRAVITY, oop.MAGNETIC):
+        K = oop.kernel_table(sub, f, mag)
+        m = rng.uniform(0, 1, sub.n)
+        r = rng.standard_normal(sub.s)
+        st = rng.integers(0, sub.s, rows)
+        cl = rng.integers(0, sub.n, cols)
+        t0 = time.perf_counter()
+        oop.forward_rows(K, sub, m, st)
+        t1 = time.perf_counter()
+        oop.adjoint_cols(K, sub, r, cl)
+        t2 = time.perf_counter()
+        t_rows += (t1 - t0) / rows * (g.nz / layers)
+        t_cols += (t2 - t1) / cols
+    # per field: 2 forward products (s rows) + 1 adjoint (n cells); t_* already sum both fields
+    per_iter = 2 * g.s * t_rows + g.n * t_cols
+    return 1.0 / per_iter, per_iter
+
+
+def run_reference(args, rank):
+    import synth
+
+    if rank != 0:
+        return
+    w = synth.joint_256()
+    vals = []
+    t0 = time.perf_counter()
+    for k in range(args.warmup + args.steps):
+        v, _ = oracle_sample(w.grid, w.mag, rows=8, cols=64, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+    wall = time.perf_counter() - t0
+    val = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: 8 forward rows (top 4 layers, scaled to 40) and 64 adjoint cells "
+                                       "per field by direct sums, extrapolated to 2 forward + 1 adjoint products "
+                                       f"per field; wall {wall:.1f} s"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "50"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def build_problem(gj, torch, prec, dev):
+    import numpy as np
+    import synth
+
+    w = synth.joint_256()
+    g = w.grid
+    ops = [gj.bttb_setup(g, "gravity", precision=prec), gj.bttb_setup(g, "magnetic", w.mag, precision=prec)]
+    dt = ops[0].dtype
+    m_true = [torch.from_numpy(x).to(dt).to(dev) for x in w.m_true]
+    d_ex = [ops[i].forward(m_true[i]) for i in range(2)]
+    sigma = [0.01 * d.abs() + 0.01 * d.abs().max() for d in d_ex]
+    dobs = [d_ex[i] + sigma[i] * torch.from_numpy(w.noise[i]).to(dt).to(dev) for i in range(2)]
+    wdep = [torch.from_numpy(gj.depth_weights(g.z_edges, b)).to(dt).to(dev) for b in (2.0, 3.0)]
+    return w, g, ops, dobs, sigma, wdep
+
+
+def solver_for(gj, torch, ops, g, dobs, sigma, wdep, kmax, dev):
+    m = [torch.zeros(g.n, dtype=ops[0].dtype, device=dev) for _ in range(2)]
+    P = gj.solver_params(p=(1, 1), lam=(2.0, 100.0), alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(5.0, 20.0),
+                         lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=kmax, stop_on_chi2=False)
+    return gj.Solver(ops, P, dobs, sigma, wdep, m), m, P
+
+
+def time_steps(torch, sv, steps, warmup, flush, profile=True, use_graph=True):
+    for _ in range(warmup):
+        flush.fill_(0.0)
+        sv.iterate(1, use_graph=use_graph)
+    torch.cuda.synchronize()
+    if profile:
+        sv.profile_read()
+    times, pn, pms = [], 0, 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0.record()
+        sv.iterate(1, use_graph=use_graph)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if profile:
+            n, ms = sv.profile_read()
+            pn += n
+            pms += ms
+    return times, pn, pms
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2112_15562_gb300 as gj
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp32", dev)
+    kmax = args.warmup + args.steps + 2
+    sv, m, P = solver_for(gj, torch, ops, g, dobs, sigma, wdep, kmax, dev)
+    sv.profile(True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    prof_mode = "events around each launch inside the captured graph"
+    try:
+        times, pn, pms = time_steps(torch, sv, args.steps, args.warmup, flush, profile=True)
+    except Exception as exc:  # graph-recorded events not readable: time the graph, then the kernel eagerly
+        prof_mode = f"separate eager pass ({type(exc).__name__})"
+        sv.profile(False)
+        times, _, _ = time_steps(torch, sv, args.steps, args.warmup, flush, profile=False)
+        pn = pms = 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    ck = clocks.stop()
+    if pn == 0:
+        sv2, _, _ = solver_for(gj, torch, ops, g, dobs, sigma, wdep, 40, dev)
+        sv2.profile(True)
+        _, pn, pms = time_steps(torch, sv2, 20, 3, flush, profile=True, use_graph=False)
+        sv2.close()
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    rep = sv.report()
+    sv.close()
+
+    # roofline of the dominant kernel: the spectrum multiply-and-sum column pass
+    o = ops[0].info
+    S_mag = o.nz * o.Ny * o.ncol * 8
+    S_grav_min = S_mag // 2  # the gravity table is even in both offsets: its spectrum is real
+    alg_bytes_launch = S_mag + S_grav_min
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    avg_ms = pms / pn if pn else None
+    achieved = alg_bytes_launch / (avg_ms * 1e-3) / 1e9 if avg_ms else None
+    roof = {"kernel": "k_col_fwd_mac (layer-summed spectrum multiply, both fields)", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+            "traffic": None, "launches_timed": pn, "avg_launch_ms": avg_ms, "timing": prof_mode,
+            "algorithmic_bytes_per_launch": alg_bytes_launch,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
+    n, s = g.n, g.s
+    iter_alg = 3 * (S_mag + S_grav_min) + 2 * 36 * n + 6 * 4 * s * 2
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 scalars)", "data": "synthetic", "config": dict(CONFIG),
+            "roofline": roof, "clocks": ck, "gpu_launches": 14 * args.steps,
+            "iteration": {"algorithmic_bytes": iter_alg,
+                          "algorithmic_GBs": iter_alg / (ms_per_step * 1e-3) / 1e9,
+                          "frac_of_hbm": iter_alg / (ms_per_step * 1e-3) / 1e9 / hbm,
+                          "wall_s": t_wall, "final_phi": rep["phi"], "S_G": rep["S_G"]}}
+    if world > 1:
+        line["config"]["parallelism"] = f"replicas x{world} (independent inversions, no collective)"
+
+    if not args.no_extras and rank == 0:
+        line["operator"] = operator_leg(torch, ops, g, dev, flush, hbm)
+        line["fp64"] = fp64_leg(gj, torch, dev, flush, value)
+        line["e2e"] = e2e_leg(gj, torch, ops, g, dobs, sigma, wdep)
+        if world == 1:
+            v, per = oracle_sample(w.grid, w.mag, rows=24, cols=400)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "24 forward rows (top 4 layers, scaled to 40) and 400 adjoint cells per "
+                                              "field by direct sums, extrapolated to one iteration "
+                                              f"({per:.0f} s per iteration)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def operator_leg(torch, ops, g, dev, flush, hbm, steps=50):
+    """G m + G^T r for both fields through gj_g_forward / gj_g_adjoint (FP32)."""
+    m = [torch.rand(g.n, device=dev) for _ in range(2)]
+    r = [torch.randn(g.s, device=dev) for _ in range(2)]
+    d = [torch.empty(g.s, device=dev) for _ in range(2)]
+    a = [torch.empty(g.n, device=dev) for _ in range(2)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name in ("forward", "adjoint"):
+        ts = []
+        for k in range(steps + 5):
+            flush.fill_(float(k))
+            e0.record()
+            for i in range(2):
+                if name == "forward":
+                    ops[i].forward(m[i], d[i])
+                else:
+                    ops[i].adjoint(r[i], a[i])
+            e1.record()
+            e1.synchronize()
+            if k >= 5:
+                ts.append(e0.elapsed_time(e1))
+        res[name] = statistics.median(ts)
+    o = ops[0].info
+    S_mag = o.nz * o.Ny * o.ncol * 8
+    per_pair = 2 * (4 * g.n + 4 * g.s) + S_mag + S_mag // 2
+    tot = res["forward"] + res["adjoint"]
+    gbs = 2 * per_pair / (tot * 1e-3) / 1e9
+    return {"forward_pair_ms": res["forward"], "adjoint_pair_ms": res["adjoint"],
+            "algorithmic_bytes_fwd_plus_adj": 2 * per_pair, "algorithmic_GBs": gbs, "frac_of_hbm": gbs / hbm,
+            "note": "both fields, standalone C-ABI calls, L2 flushed, medians of 50"}
+
+
+def fp64_leg(gj, torch, dev, flush, v32, steps=8, warmup=2):
+    w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp64", dev)
+    sv, m, P = solver_for(gj, torch, ops, g, dobs, sigma, wdep, steps + warmup + 2, dev)
+    times, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
+    sv.close()
+    for o in ops:
+        o.close()
+    ms = sum(times) / steps
+    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "fp32_speedup": v32 / (1e3 / ms), "dtype": "f64 (plain FP64 form)"}
+
+
+def e2e_leg(gj, torch, ops, g, dobs, sigma, wdep, iters=20):
+    """The host-API solve (numpy in, numpy out): copies, solver setup, ``iters``
+    iterations and the copy of both models back, timed on the wall clock."""
+    import numpy as np
+
+    host = [x.cpu().numpy() for x in dobs] + [x.cpu().numpy() for x in sigma] + [x.cpu().numpy() for x in wdep]
+    m0 = [np.zeros(g.n, dtype=np.float32), np.zeros(g.n, dtype=np.float32)]
+    P = gj.solver_params(p=(1, 1), lam=(2.0, 100.0), alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(5.0, 20.0),
+                         lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=iters, stop_on_chi2=False)
+    gj.rrcg_joint_solve_host(ops, P, host[0:2], host[2:4], host[4:6], m0)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    models, rep, bin_, bout = gj.rrcg_joint_solve_host(ops, P, host[0:2], host[2:4], host[4:6], m0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": UNIT, "h2d_bytes_per_step": bin_ / iters, "d2h_bytes_per_step": bout / iters,
+            "iterations_per_call": iters, "call_s": dt,
+            "note": "gj_rrcg_joint_solve through the host API: pinned H2D of data, sigma, weights and start models, "
+                    "solver creation and graph capture, the iterations, D2H of both models"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

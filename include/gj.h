@@ -81,6 +81,7 @@ typedef struct {
     gj_precision precision;
     int64_t spectrum_bytes;  /* device bytes of the stored layer spectra */
     int64_t workspace_bytes; /* device bytes of the per-op workspace */
+    int fast_path;           /* 1: the specialised 512 x 512 kernels serve this op */
 } gj_op_info_t;
 
 /*
@@ -97,7 +98,7 @@ typedef struct {
  * product).  `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
  * Synchronous with respect to the host on return (the op is ready).
  * Returns GJ_ERR_ARG for invalid sizes, GJ_ERR_UNSUPPORTED for a padded size
- * above 4096 or with a larger prime factor, GJ_ERR_OOM if device memory runs
+ * above 2048 or with a larger prime factor, GJ_ERR_OOM if device memory runs
  * out.  On success *out owns device memory until gj_op_destroy.
  */
 gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag,

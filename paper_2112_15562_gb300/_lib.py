@@ -34,7 +34,8 @@ class Mag(ct.Structure):
 class OpInfo(ct.Structure):
     _fields_ = [("sx", ct.c_int), ("sy", ct.c_int), ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
                 ("Nx", ct.c_int), ("Ny", ct.c_int), ("ncol", ct.c_int), ("field", ct.c_int),
-                ("precision", ct.c_int), ("spectrum_bytes", ct.c_int64), ("workspace_bytes", ct.c_int64)]
+                ("precision", ct.c_int), ("spectrum_bytes", ct.c_int64), ("workspace_bytes", ct.c_int64),
+                ("fast_path", ct.c_int)]
 
 
 class RRCGParams(ct.Structure):

@@ -275,6 +275,19 @@ struct LoadPlain {  // a = x0[la*pitch + j], b = x1[lb*pitch + j]
         a = x0[(size_t)la * pitch + j];
         b = hb ? x1[(size_t)lb * pitch + j] : R(0);
     }
+    // elements j0 + k * stride (k < K) below n; zero beyond
+    template <int K>
+    __device__ __forceinline__ void fetch_batch(int la, int lb, bool hb, int j0, int stride, int n, R (&a)[K],
+                                                R (&b)[K]) const {
+        const R *pa = x0 + (size_t)la * pitch;
+        const R *pb = x1 + (size_t)lb * pitch;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            a[k] = j < n ? pa[j] : R(0);
+            b[k] = (hb && j < n) ? pb[j] : R(0);
+        }
+    }
     __device__ __forceinline__ void flush(double *) const {}
 };
 
@@ -287,6 +300,18 @@ struct StorePlain {
     __device__ __forceinline__ void store(int la, int lb, bool hb, int j, R a, R b) const {
         y0[(size_t)la * pitch + j] = a;
         if (hb) y1[(size_t)lb * pitch + j] = b;
+    }
+    template <int K>
+    __device__ __forceinline__ void store_batch(int la, int lb, bool hb, int j0, int stride, int n, const R (&a)[K],
+                                                const R (&b)[K]) const {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            if (j < n) {
+                y0[(size_t)la * pitch + j] = a[k];
+                if (hb) y1[(size_t)lb * pitch + j] = b[k];
+            }
+        }
     }
     __device__ __forceinline__ void flush(double *) const {}
 };

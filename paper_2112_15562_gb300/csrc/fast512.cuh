@@ -1,0 +1,628 @@
+// Specialised kernels for a 512 x 512 BCCB embedding with at most 256 prisms and
+// 256 stations per direction (the zero-padded half of every transform is never
+// read or computed).
+//
+// Warp FFT.  A pruned 512-point transform of 256 inputs x[n] splits into its even
+// and odd outputs, X[2k + h] = FFT256(x[n] W512^(h n))[k]; half-warp h computes one
+// of them.  Each 256-point transform is 16 x 16: lane l holds x[l + 16 j]
+// (j < 16), takes a 16-point DFT over j, multiplies by W256^(l k2), transposes
+// through a swizzled shared-memory tile and takes a second 16-point DFT over l.
+// Lane (h, k2) then holds X[2(k2 + 16 k1) + h] = X[lambda + 32 k1] in register k1,
+// lambda = 2 k2 + h.  The inverse runs the same steps backwards and returns
+// y[n], n < 256, with the even/odd halves combined across the two half-warps.
+//
+// Layouts (per field): row-pass output Zt[r][kx][iy] (kx < 257, iy < 256),
+// spectra St[r][kx][ky] (ky < 512), inverse-column output Wt[kx][jy].  Every
+// column a warp streams is contiguous (2 KB or 4 KB), fetched with 1-D TMA bulk
+// copies into a per-warp ring completed by mbarriers.
+#pragma once
+#include "bttb_kernels.cuh"
+#include "gj.h"
+
+namespace gj {
+namespace f512 {
+
+constexpr int N = 512, H = 256, NC = 257;
+constexpr int WARPS = 8;          // warps per CTA in every fast kernel
+constexpr int STAGES = 3;         // TMA ring depth of the column kernels
+constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
+
+// ---------------------------------------------------------------------------
+// small DFTs in registers
+
+template <typename R> struct K16;
+template <> struct K16<float> {
+    static __device__ __forceinline__ float c1() { return 0.92387953251128675613f; }
+    static __device__ __forceinline__ float s1() { return 0.38268343236508977173f; }
+    static __device__ __forceinline__ float r2() { return 0.70710678118654752440f; }
+};
+template <> struct K16<double> {
+    static __device__ __forceinline__ double c1() { return 0.92387953251128675613; }
+    static __device__ __forceinline__ double s1() { return 0.38268343236508977173; }
+    static __device__ __forceinline__ double r2() { return 0.70710678118654752440; }
+};
+
+// multiply by W16^e (forward) or W16^-e (inverse) for e in {0,1,2,3,4,6,9}
+template <typename R, bool INV, int E>
+__device__ __forceinline__ cpx<R> w16(cpx<R> a) {
+    using C = cpx<R>;
+    const R c1 = K16<R>::c1(), s1 = K16<R>::s1(), r2 = K16<R>::r2();
+    const R sg = INV ? R(1) : R(-1);  // sign of the imaginary part of the root
+    if constexpr (E == 0) return a;
+    else if constexpr (E == 1) { const R wr = c1, wi = sg * s1; return mk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr); }
+    else if constexpr (E == 2) { const R wr = r2, wi = sg * r2; return mk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr); }
+    else if constexpr (E == 3) { const R wr = s1, wi = sg * c1; return mk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr); }
+    else if constexpr (E == 4) return mul_mi<C, INV>(a);
+    else if constexpr (E == 6) { const R wr = -r2, wi = sg * r2; return mk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr); }
+    else { static_assert(E == 9, "w16"); const R wr = -c1, wi = -sg * s1; return mk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr); }
+}
+
+template <typename R, bool INV, int N2>
+__device__ __forceinline__ void tw_col(cpx<R> (&y)[16]) {
+    // y[n2 + 4 k1] *= W16^(n2 k1)
+    y[N2 + 4] = w16<R, INV, N2 * 1>(y[N2 + 4]);
+    y[N2 + 8] = w16<R, INV, N2 * 2>(y[N2 + 8]);
+    y[N2 + 12] = w16<R, INV, N2 * 3>(y[N2 + 12]);
+}
+
+// 16-point DFT in place, natural order in and out.
+template <typename R, bool INV>
+__device__ __forceinline__ void dft16(cpx<R> (&x)[16]) {
+    using C = cpx<R>;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<R, INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+    tw_col<R, INV, 1>(x);
+    tw_col<R, INV, 2>(x);
+    tw_col<R, INV, 3>(x);
+    // now x[n2 + 4 k1] = Y[n2][k1]; DFT4 over n2 gives X[k1 + 4 k2]
+    C o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C a0 = x[4 * k1 + 0], a1 = x[4 * k1 + 1], a2 = x[4 * k1 + 2], a3 = x[4 * k1 + 3];
+        dft4<R, INV>(a0, a1, a2, a3);
+        o[k1 + 0] = a0; o[k1 + 4] = a1; o[k1 + 8] = a2; o[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = o[i];
+}
+
+// cos(pi j / 16) for j = 0..8 (W32^j = cos(pi j/16) - i sin(pi j/16))
+__host__ __device__ constexpr double cos_pi16(int j) {
+    return j == 0 ? 1.0
+         : j == 1 ? 0.98078528040323044913
+         : j == 2 ? 0.92387953251128675613
+         : j == 3 ? 0.83146961230254523708
+         : j == 4 ? 0.70710678118654752440
+         : j == 5 ? 0.55557023301960222474
+         : j == 6 ? 0.38268343236508977173
+         : j == 7 ? 0.19509032201612826785
+                  : 0.0;
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> w32c(int j) {  // W32^j for 0 <= j < 16 (j known at compile time)
+    const double c = j <= 8 ? cos_pi16(j) : -cos_pi16(16 - j);
+    const double sn = j <= 8 ? cos_pi16(8 - j) : cos_pi16(j - 8);
+    return mk<cpx<R>>((R)c, (R)(-sn));
+}
+
+// Per-lane twiddles: W256^(l k) = lo[k & 3] * hi[k >> 2] with l = lane & 15,
+// and the odd-half pre-twiddle W512^(l + 16 j) = pre * W32^j.
+template <typename R>
+struct LaneTw {
+    cpx<R> lo[4], hi[4], pre;
+    __device__ void load(const cpx<R> *tw512) {  // tw512[k] = W512^k
+        const int l = threadIdx.x & 15;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            lo[k] = tw512[(2 * l * k) & 511];
+            hi[k] = tw512[(8 * l * k) & 511];
+        }
+        pre = tw512[l];
+    }
+    template <bool INV> __device__ __forceinline__ cpx<R> mul256(cpx<R> a, int k) const {
+        const cpx<R> w = cmul(lo[k & 3], hi[k >> 2]);
+        return INV ? cmulc(a, w) : cmul(a, w);
+    }
+};
+
+// swizzled 16 x 16 tile of one half-warp: entry (row, col) at row*16 + (col ^ row)
+__device__ __forceinline__ int swz(int row, int col) { return row * 16 + (col ^ row); }
+
+// Forward pruned 512-point transform.  In: v[j] = x[l + 16 j] (both halves).
+// Out: lane (h, k2) v[k1] = X[lambda + 32 k1].  buf: this warp's 512-entry tile.
+template <typename R>
+__device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const LaneTw<R> &tw) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    cpx<R> *t = buf + h * 256;
+    if (h) {
+        const cpx<R> p = tw.pre;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], cmul(p, w32c<R>(j)));
+    }
+    dft16<R, false>(v);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) v[k] = tw.template mul256<false>(v[k], k);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t[swz(l, k)] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = t[swz(r, l)];
+    dft16<R, false>(v);
+}
+
+// Inverse: in lane (h, k2) v[k1] = Y[lambda + 32 k1].  Out (unnormalised): every
+// lane of both halves holds y[n] for n = l + 16 j with j in [8h, 8h + 8):
+// out[jj] = y[l + 16 (8h + jj)], jj < 8.
+template <typename R>
+__device__ __forceinline__ void inv512(cpx<R> (&v)[16], cpx<R> *buf, const LaneTw<R> &tw, cpx<R> (&out)[8]) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, k2 = lane & 15;
+    cpx<R> *t = buf + h * 256;
+    dft16<R, true>(v);  // over k1 -> index l
+#pragma unroll
+    for (int l = 1; l < 16; ++l) v[l] = tw.template mul256<true>(v[l], l);
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) t[swz(k2, l)] = v[l];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = t[swz(r, k2)];
+    dft16<R, true>(v);  // over k2 -> j ; now v[j] = z_h[k2 + 16 j] (this lane's l = k2)
+    // y[n] = z_0[n] + W512^-n z_1[n]
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        cpx<R> o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[j].x, 16);
+        o.y = __shfl_xor_sync(0xffffffffu, v[j].y, 16);
+        const bool mine = (j >> 3) == h;
+        if (mine) {
+            const cpx<R> z0 = h ? o : v[j];
+            const cpx<R> z1 = h ? v[j] : o;
+            const cpx<R> w = cmul(tw.pre, w32c<R>(j));  // W512^(l + 16 j)
+            out[j & 7] = cadd(z0, cmulc(z1, w));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(dst)),
+        "l"(src), "r"(bytes), "r"(s_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(s_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; returns false (and records an error) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    for (long long i = 0; i < kSpinLimit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    if (err) atomicExch(err, GJ_ERR_TIMEOUT);
+    return false;
+}
+
+// After a timed-out wait at item t_fail, wait (bounded) for the copies this warp
+// issued and has not consumed (items t_fail .. t_fail + STAGES - 1) so that no bulk
+// copy lands in shared memory after the CTA exits.
+__device__ __forceinline__ void drain(uint64_t *bars, long long t_fail, long long t0, long long t1, int *err) {
+    for (long long t = t_fail; t < t1 && t < t_fail + STAGES; ++t) {
+        const int s = (int)((t - t0) % STAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+        mbar_wait(bars + s, par, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Segmentation of the flattened (field, kx, layer) sequence over the warps of a
+// persistent grid: warp w takes [T w / Wt, T (w+1) / Wt).
+
+__device__ __host__ __forceinline__ long long seg_warps(long long warps, long long T) { return warps < T ? warps : T; }
+__device__ __host__ __forceinline__ long long seg_begin(long long w, long long T, long long Wt) { return (w * T) / Wt; }
+// the warp whose segment contains item t
+__device__ __host__ __forceinline__ long long seg_owner(long long t, long long T, long long Wt) {
+    return ((t + 1) * Wt + T - 1) / T - 1;
+}
+
+template <typename R>
+struct View2 {  // the two fields of a launch (field 1 unused in single-field launches)
+    OpView<R> op[2];
+    cpx<R> *P[2];   // [NC][slots][512] layer-sum partials
+    int *cnt[2];    // [NC] arrival counters (zero between launches)
+    int slots;      // partial slots per column
+    int nfield;
+    int *err;
+};
+
+// ---------------------------------------------------------------------------
+// Row pass (x direction), real lines -> half spectra in the transposed layout.
+// CTA: WARPS warps x 2 complex transforms = 16 transforms.  Joint mode: transform
+// f packs line (base + f) of field 0 (real) and field 1 (imaginary); single mode:
+// lines (base + 2f, base + 2f + 1) of field 0.  lpl = lines per layer (ny or sy).
+template <typename R, class Pro>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_row_fwd512(View2<R> V, int joint, int nlines, int lpl, int n_in,
+                                                           int out_is_W, Pro pro, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);         // [16][N + 1]
+    C *xb = tile + 16 * (N + 1);                          // per warp 512
+    C *tws = xb + WARPS * N;                              // W512 table
+    __shared__ double red[32];
+    const OpView<R> &op0 = V.op[0];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = op0.twx[i];
+    pro.init();
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load(tws);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int per_tile = joint ? 16 : 32;
+    const int base = blockIdx.x * per_tile;
+    C *buf = xb + warp * N;
+    for (int s = 0; s < 2; ++s) {
+        const int f = warp * 2 + s;
+        int la, lb;
+        bool ha, hb;
+        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
+        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
+        // all lanes fetch elements lane + 32 i (contiguous), then redistribute
+        R a[8], b[8];
+        if (ha) {
+            pro.template fetch_batch<8>(la, lb, hb, lane, 32, n_in, a, b);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
+        __syncwarp();
+        C v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = buf[l + 16 * j];
+        fwd512<R>(v, buf, tw);
+        // natural-order spectrum of this transform into the staging tile
+        const int lam = 2 * l + h;
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + lam + 32 * k1] = v[k1];
+    }
+    __syncthreads();
+    // split into the two real half spectra and write Zt[r][kx][iy]
+    for (int it = threadIdx.x; it < NC * 16; it += blockDim.x) {
+        const int f = it & 15, kx = it >> 4;
+        const C zk = tile[f * (N + 1) + kx];
+        const C zm = tile[f * (N + 1) + ((N - kx) & (N - 1))];
+        const C A = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        const C B = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        int la, lb;
+        bool ha, hb;
+        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
+        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
+        if (ha) {
+            const int r = la / lpl, iy = la - r * lpl;
+            C *o = out_is_W ? V.op[0].W : V.op[0].Z;
+            o[((size_t)r * NC + kx) * H + iy] = A;
+        }
+        if (hb) {
+            const int fb = joint ? 1 : 0;
+            const int r = lb / lpl, iy = lb - r * lpl;
+            C *o = out_is_W ? V.op[fb].W : V.op[fb].Z;
+            o[((size_t)r * NC + kx) * H + iy] = B;
+        }
+    }
+    pro.flush(red);
+}
+
+// ---------------------------------------------------------------------------
+// Inverse row pass: half spectra in[r][kx][iy] -> real lines, cropped to n_out.
+template <typename R, class Epi>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_row_inv512(View2<R> V, int joint, int nlines, int lpl, int n_out,
+                                                           int in_is_W, Epi epi, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][33]
+    C *xb = tile + NC * 33;
+    C *tws = xb + WARPS * N;
+    __shared__ double red[32];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
+    epi.init();
+    const int per_tile = joint ? 16 : 32;
+    const int base = blockIdx.x * per_tile;
+    // stage: source column s < 32 -> (field, line); joint: s = 16*field + f, line base + f
+    {
+        // this thread's source column s is fixed; issue 8 loads before storing any
+        const int s = threadIdx.x & 31;
+        const int fld = joint ? (s >> 4) : 0;
+        const int line = joint ? base + (s & 15) : base + s;
+        const bool ok = line < nlines;
+        const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
+        const C *in = (in_is_W ? V.op[fld].W : V.op[fld].Z) + (size_t)r * NC * H + iy;
+        const int kx0 = threadIdx.x >> 5, kstep = blockDim.x >> 5;
+        for (int kb = kx0; kb < NC; kb += 8 * kstep) {
+            C val[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int kx = kb + u * kstep;
+                val[u] = (ok && kx < NC) ? in[(size_t)kx * H] : czero<C>();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int kx = kb + u * kstep;
+                if (kx < NC) tile[kx * 33 + s] = val[u];
+            }
+        }
+    }
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load(tws);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    C *buf = xb + warp * N;
+    for (int s2 = 0; s2 < 2; ++s2) {
+        const int f = warp * 2 + s2;
+        const int sa = joint ? f : 2 * f;
+        const int sb = joint ? 16 + f : 2 * f + 1;
+        C v[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const int k = lam + 32 * k1;
+            const bool lo = k <= H;
+            const int kk = lo ? k : N - k;
+            C A = tile[kk * 33 + sa], B = tile[kk * 33 + sb];
+            if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+            v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+        }
+        C out[8];
+        inv512<R>(v, buf, tw, out);
+        int la, lb;
+        bool ha, hb;
+        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
+        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
+        // natural order through the warp tile, then contiguous batches per lane
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
+        __syncwarp();
+        if (ha) {
+            R a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const C y = buf[lane + 32 * i];
+                a[i] = y.x;
+                b[i] = y.y;
+            }
+            epi.template store_batch<8>(la, lb, hb, lane, 32, n_out, a, b);
+        }
+    }
+    epi.flush(red);
+}
+
+// ---------------------------------------------------------------------------
+// Forward column pass: for each (field, kx), Y = sum_r St_r[kx] . FFT512(Zt_r[kx]),
+// then W[kx][jy] = IFFT512(Y)[jy] for jy < sy.  Persistent warps take balanced
+// contiguous segments of the (field, kx, r) sequence; a column split across warps
+// is summed in segment order by the last warp to finish it.
+template <typename R>
+__global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int ZB = H * sizeof(C), TB = N * sizeof(C);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    unsigned char *wbase = smem_raw + (size_t)warp * (STAGES * (ZB + TB) + N * sizeof(C));
+    C *zs = reinterpret_cast<C *>(wbase);                          // STAGES x 256
+    C *ts = reinterpret_cast<C *>(wbase + STAGES * ZB);            // STAGES x 512
+    C *xbuf = reinterpret_cast<C *>(wbase + STAGES * (ZB + TB));   // 512
+    C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * (ZB + TB) + N * sizeof(C)));
+    __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twy[i];
+    if (lane == 0)
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
+    mbar_fence_init();
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load(tws);
+    const int nz = V.op[0].nz, sy = V.op[0].sy;
+    const long long T = (long long)V.nfield * NC * nz;
+    // at most T warps take part, so that every segment holds at least one item
+    const long long Wt = seg_warps((long long)gridDim.x * WARPS, T);
+    const long long w = (long long)blockIdx.x * WARPS + warp;
+    if (w >= Wt) return;
+    const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
+    const int lam = 2 * l + h;
+    auto issue = [&](long long t) {
+        const int s = (int)((t - t0) % STAGES);
+        const int r = (int)(t % nz);
+        const long long col = t / nz;
+        const int fld = (int)(col / NC), kx = (int)(col % NC);
+        const OpView<R> &op = V.op[fld];
+        mbar_expect(&bars[warp][s], ZB + TB);
+        bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
+        bulk_load(ts + s * N, op.spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+    };
+    if (lane == 0)
+        for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
+    C acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = czero<C>();
+    bool ok = true;
+    long long t_fail = t1;
+    long long seg_start = t0;
+    for (long long t = t0; t < t1 && ok; ++t) {
+        const int s = (int)((t - t0) % STAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
+        if (!ok) { t_fail = t; break; }
+        C v[16], tv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = zs[s * H + l + 16 * j];
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) tv[k1] = ts[s * N + lam + 32 * k1];
+        __syncwarp();
+        if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
+        fwd512<R>(v, xbuf, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], tv[k1]));
+        const int r = (int)(t % nz);
+        if (r == nz - 1 || t == t1 - 1) {
+            // end of this warp's part of column `col`
+            const long long col = t / nz;
+            const int fld = (int)(col / NC), kx = (int)(col % NC);
+            const OpView<R> &op = V.op[fld];
+            const long long cb = col * nz, ce = cb + nz - 1;
+            const bool whole = (seg_start <= cb) && (t == ce);
+            if (!whole) {
+                const long long wf = seg_owner(cb, T, Wt), wl = seg_owner(ce, T, Wt);
+                const int slot = (int)(w - wf), nslots = (int)(wl - wf + 1);
+                C *Pc = V.P[fld] + (size_t)kx * V.slots * N;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) Pc[(size_t)slot * N + lam + 32 * k1] = acc[k1];
+                __threadfence();
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(V.cnt[fld] + kx, 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == nslots - 1) {
+                    __threadfence();
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+                    for (int sl = 0; sl < nslots; ++sl) {
+#pragma unroll
+                        for (int k1 = 0; k1 < 16; ++k1)
+                            acc[k1] = cadd(acc[k1], __ldcg(Pc + (size_t)sl * N + lam + 32 * k1));
+                    }
+                    if (lane == 0) V.cnt[fld][kx] = 0;
+                } else {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+                    seg_start = t + 1;
+                    continue;
+                }
+            }
+            C out[8];
+            inv512<R>(acc, xbuf, tw, out);
+            C *Wc = op.W + (size_t)kx * H;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int n = l + 16 * (8 * h + jj);
+                if (n < sy) Wc[n] = out[jj];
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+            seg_start = t + 1;
+        }
+    }
+    if (!ok) drain(bars[warp], t_fail, t0, t1, V.err);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint column pass: for each (field, kx, r),
+// Zt_r[kx][iy] = IFFT512(conj(St_r[kx]) . FFT512(Wt[kx]))[iy], iy < ny.
+template <typename R>
+__global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TB = N * sizeof(C);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    unsigned char *wbase = smem_raw + (size_t)warp * (STAGES * TB + N * sizeof(C));
+    C *ts = reinterpret_cast<C *>(wbase);
+    C *xbuf = reinterpret_cast<C *>(wbase + STAGES * TB);
+    C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * TB + N * sizeof(C)));
+    __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twy[i];
+    if (lane == 0)
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
+    mbar_fence_init();
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load(tws);
+    const int nz = V.op[0].nz, ny = V.op[0].ny;
+    const long long T = (long long)V.nfield * NC * nz;
+    // at most T warps take part, so that every segment holds at least one item
+    const long long Wt = seg_warps((long long)gridDim.x * WARPS, T);
+    const long long w = (long long)blockIdx.x * WARPS + warp;
+    if (w >= Wt) return;
+    const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
+    const int lam = 2 * l + h;
+    auto issue = [&](long long t) {
+        const int s = (int)((t - t0) % STAGES);
+        const int r = (int)(t % nz);
+        const long long col = t / nz;
+        const int fld = (int)(col / NC), kx = (int)(col % NC);
+        mbar_expect(&bars[warp][s], TB);
+        bulk_load(ts + s * N, V.op[fld].spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+    };
+    if (lane == 0)
+        for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
+    C vh[16];
+    long long cur_col = -1;
+    bool ok = true;
+    long long t_fail = t1;
+    for (long long t = t0; t < t1 && ok; ++t) {
+        const long long col = t / nz;
+        const int r = (int)(t % nz);
+        const int fld = (int)(col / NC), kx = (int)(col % NC);
+        const OpView<R> &op = V.op[fld];
+        if (col != cur_col) {
+            // V^ = FFT512 of the residual column (rows >= sy are zero)
+            const C *Wc = op.W + (size_t)kx * H;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) vh[j] = Wc[l + 16 * j];
+            fwd512<R>(vh, xbuf, tw);
+            cur_col = col;
+        }
+        const int s = (int)((t - t0) % STAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
+        if (!ok) { t_fail = t; break; }
+        C v[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], ts[s * N + lam + 32 * k1]);
+        __syncwarp();
+        if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
+        C out[8];
+        inv512<R>(v, xbuf, tw, out);
+        C *Zc = op.Z + ((size_t)r * NC + kx) * H;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int n = l + 16 * (8 * h + jj);
+            if (n < ny) Zc[n] = out[jj];
+        }
+    }
+    if (!ok) drain(bars[warp], t_fail, t0, t1, V.err);
+}
+
+// shared-memory bytes of each kernel
+template <typename R> inline size_t smem_row_fwd() { return (size_t)(16 * (N + 1) + WARPS * N + N) * sizeof(cpx<R>); }
+template <typename R> inline size_t smem_row_inv() { return (size_t)(NC * 33 + WARPS * N + N) * sizeof(cpx<R>); }
+template <typename R> inline size_t smem_col_fwd() {
+    return (size_t)WARPS * (STAGES * (H + N) + N) * sizeof(cpx<R>) + N * sizeof(cpx<R>);
+}
+template <typename R> inline size_t smem_col_adj() {
+    return (size_t)WARPS * (STAGES * N + N) * sizeof(cpx<R>) + N * sizeof(cpx<R>);
+}
+
+}  // namespace f512
+}  // namespace gj

@@ -26,6 +26,14 @@ struct gj_op {
     size_t spec_bytes = 0, ws_bytes = 0;
     // launch shapes
     int P_row = 8, C_col = 8, L_grp = 4;
+    // 512 x 512 fast path (FP32, <= 256 prisms and stations per direction):
+    // transposed spectra and intermediates, layer-sum partials and counters
+    bool fast = false;
+    void *P = nullptr;     // [ncol][slots][512] complex
+    int *cnt = nullptr;    // [ncol] arrival counters
+    int *err = nullptr;    // device error word (bounded waits)
+    int slots = 0;
+    int col_grid = 0;      // CTAs of the persistent column kernels
 };
 
 namespace gj {
@@ -43,6 +51,10 @@ int pick_col_tile(int Ny, size_t csize, int nbuf);
 
 template <typename R> struct OpView;
 template <typename R> OpView<R> view_of(const gj_op *op);
+
+// fast-path helpers (setup.cu)
+bool fast_eligible(const gj_op *op);
+int fast_slots(int nfield, int nz, int grid_ctas);
 
 // enqueue products (matvec.cu)
 gj_status forward_enqueue(const gj_op *op, const void *m, void *d, cudaStream_t s);

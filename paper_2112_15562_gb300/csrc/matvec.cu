@@ -1,5 +1,6 @@
 // G m and G^T r of one field (Sec. 2.7.1): the C-ABI entry points and the launch
 // sequences shared with the solver.
+#include "fast_launch.cuh"
 #include "view.cuh"
 
 namespace gj {
@@ -61,15 +62,40 @@ static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
                                                                      StorePlain<R>{g, g, o->nx}, nullptr);
 }
 
+// 512 x 512 fast path: rows -> persistent layer-summed columns -> inverse rows
+static void fast_forward(const gj_op *o, const float *m, float *d, cudaStream_t st) {
+    using namespace f512;
+    View2<float> V = make_view2<float>(o, nullptr);
+    set_row_fwd_attr<float, LoadPlain<float>>();
+    set_row_inv_attr<float, StorePlain<float>>();
+    set_col_attr<float>();
+    row_fwd<float>(V, 0, o->nz * o->ny, o->ny, o->nx, 0, LoadPlain<float>{m, m, o->nx}, nullptr, st);
+    col_fwd<float>(V, o->col_grid, nullptr, st);
+    row_inv<float>(V, 0, o->sy, o->sy, o->sx, 1, StorePlain<float>{d, d, o->sx}, nullptr, st);
+}
+
+static void fast_adjoint(const gj_op *o, const float *r, float *g, cudaStream_t st) {
+    using namespace f512;
+    View2<float> V = make_view2<float>(o, nullptr);
+    set_row_fwd_attr<float, LoadPlain<float>>();
+    set_row_inv_attr<float, StorePlain<float>>();
+    set_col_attr<float>();
+    row_fwd<float>(V, 0, o->sy, o->sy, o->sx, 1, LoadPlain<float>{r, r, o->sx}, nullptr, st);
+    col_adj<float>(V, o->col_grid, nullptr, st);
+    row_inv<float>(V, 0, o->nz * o->ny, o->ny, o->nx, 0, StorePlain<float>{g, g, o->nx}, nullptr, st);
+}
+
 gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {
-    if (o->prec == GJ_FP64) launch_forward<double>(o, (const double *)m, (double *)d, st);
+    if (o->fast) fast_forward(o, (const float *)m, (float *)d, st);
+    else if (o->prec == GJ_FP64) launch_forward<double>(o, (const double *)m, (double *)d, st);
     else launch_forward<float>(o, (const float *)m, (float *)d, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GJ_OK : cuda_fail(e, "g_forward launch");
 }
 
 gj_status adjoint_enqueue(const gj_op *o, const void *r, void *g, cudaStream_t st) {
-    if (o->prec == GJ_FP64) launch_adjoint<double>(o, (const double *)r, (double *)g, st);
+    if (o->fast) fast_adjoint(o, (const float *)r, (float *)g, st);
+    else if (o->prec == GJ_FP64) launch_adjoint<double>(o, (const double *)r, (double *)g, st);
     else launch_adjoint<float>(o, (const float *)r, (float *)g, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GJ_OK : cuda_fail(e, "g_adjoint launch");

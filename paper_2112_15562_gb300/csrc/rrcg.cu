@@ -18,8 +18,10 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
+#include "fast_launch.cuh"
 #include "view.cuh"
 
 namespace gj {
@@ -73,6 +75,20 @@ __device__ __forceinline__ R weight(const FieldVecs<R> &F, int i, int p, R eps2,
     return w;
 }
 
+// The L1 reweighting factor of Eq. WL and its reciprocal for p = 1 (1 for p = 2):
+// ((m - m_apr)^2 + eps^2)^(-1/4) and ((m - m_apr)^2 + eps^2)^(1/4).
+template <typename R>
+__device__ __forceinline__ void lp_factors(int p, R d, R eps2, R &wl, R &inv_wl) {
+    if (p == 1) {
+        const R q = sqrt(d * d + eps2);
+        wl = rsqrt_t<R>(q);
+        inv_wl = sqrt(q);
+    } else {
+        wl = R(1);
+        inv_wl = R(1);
+    }
+}
+
 // Forward of m with the pending model update (RRCG:7-8 and the bounds) and the
 // Gramian sums of the updated models.
 template <typename R>
@@ -112,6 +128,56 @@ struct ProModel {
         a = mv[0];
         b = mv[1];
     }
+    // batched form: every load of the K elements is issued before any store
+    template <int K>
+    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+        const size_t c0 = (size_t)la * nx;
+        const int r = la / ny;
+        R mv[2][K], pv[2][K], wh[2][K], ma[2][K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+            const size_t c = c0 + j;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                mv[i][k] = ok ? F.m[i][c] : R(0);
+                pv[i][k] = (ok && upd) ? F.p[i][c] : R(0);
+                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c] : R(1);
+                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c] : R(0);
+            }
+        }
+        if (upd) {
+            R iwd[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) iwd[i] = R(1) / F.wdep[i][r];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k * stride;
+                if (j >= n) continue;
+                const size_t c = c0 + j;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    R wl, iwl;
+                    lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
+                    R inv_w = iwl * iwd[i];
+                    if (F.whard[i]) inv_w /= wh[i][k];
+                    R mi = mv[i][k] - s[i] * pv[i][k] * inv_w;
+                    mi = fmin(fmax(mi, lo[i]), hi[i]);
+                    F.m[i][c] = mi;
+                    mv[i][k] = mi;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            acc[0] += mv[0][k] * mv[0][k];
+            acc[1] += mv[1][k] * mv[1][k];
+            acc[2] += mv[0][k] * mv[1][k];
+            a[k] = mv[0][k];
+            b[k] = mv[1][k];
+        }
+    }
     __device__ void flush(double *red) { block_accumulate<3>(acc, S->G, red); }
 };
 
@@ -133,6 +199,34 @@ struct EpiResidual {
             F.v[i][t] = w * rt;
         }
     }
+    template <int K>
+    __device__ __forceinline__ void store_batch(int la, int, bool, int j0, int stride, int n, const R (&a)[K],
+                                                const R (&b)[K]) {
+        const size_t t0 = (size_t)la * sx;
+        R w[2][K], d[2][K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                w[i][k] = ok ? F.wd[i][t0 + j] : R(0);
+                d[i][k] = ok ? F.dobs[i][t0 + j] : R(0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            if (j >= n) continue;
+            const R y[2] = {a[k], b[k]};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const R rt = w[i][k] * (y[i] - d[i][k]);
+                acc[i] += rt * rt;
+                F.v[i][t0 + j] = w[i][k] * rt;
+            }
+        }
+    }
     __device__ void flush(double *red) { block_accumulate<2>(acc, S->phi, red); }
 };
 
@@ -145,6 +239,16 @@ struct LoadPair {
     __device__ __forceinline__ void fetch(int la, int lb, bool, int j, R &a, R &b) const {
         a = x0[(size_t)la * pitch + j];
         b = x1[(size_t)lb * pitch + j];
+    }
+    template <int K>
+    __device__ __forceinline__ void fetch_batch(int la, int lb, bool, int j0, int stride, int n, R (&a)[K],
+                                                R (&b)[K]) const {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            a[k] = j < n ? x0[(size_t)la * pitch + j] : R(0);
+            b[k] = j < n ? x1[(size_t)lb * pitch + j] : R(0);
+        }
     }
     __device__ void flush(double *) {}
 };
@@ -177,6 +281,44 @@ struct EpiGradient {
             const R li = g[i] / w + alpha[i] * (w * mm[i] - w * ma) + lam[i] * lG[i];
             F.l[i][c] = li;
             acc[i] += li * li;
+        }
+    }
+    template <int K>
+    __device__ __forceinline__ void store_batch(int la, int, bool, int j0, int stride, int n, const R (&a)[K],
+                                                const R (&b)[K]) {
+        const size_t c0 = (size_t)la * nx;
+        const int r = la / ny;
+        R mv[2][K], wh[2][K], ma[2][K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                mv[i][k] = ok ? F.m[i][c0 + j] : R(0);
+                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
+                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
+            }
+        }
+        R wd[2], iwd[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) { wd[i] = F.wdep[i][r]; iwd[i] = R(1) / wd[i]; }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            if (j >= n) continue;
+            const R lG[2] = {g22 * mv[0][k] - g12 * mv[1][k], g11 * mv[1][k] - g12 * mv[0][k]};
+            const R g[2] = {a[k], b[k]};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                R wl, iwl;
+                lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
+                R w = wd[i] * wl, inv_w = iwl * iwd[i];
+                if (F.whard[i]) { w *= wh[i][k]; inv_w /= wh[i][k]; }
+                const R li = g[i] * inv_w + alpha[i] * w * (mv[i][k] - ma[i][k]) + lam[i] * lG[i];
+                F.l[i][c0 + j] = li;
+                acc[i] += li * li;
+            }
         }
     }
     __device__ void flush(double *red) { block_accumulate<2>(acc, S->ll, red); }
@@ -219,6 +361,50 @@ struct ProDirection {
         a = x[0];
         b = x[1];
     }
+    template <int K>
+    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+        const size_t c0 = (size_t)la * nx;
+        const int r = la / ny;
+        R lv[2][K], pv[2][K], mv[2][K], wh[2][K], ma[2][K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                lv[i][k] = ok ? F.l[i][c0 + j] : R(0);
+                pv[i][k] = (ok && !first) ? F.p[i][c0 + j] : R(0);
+                mv[i][k] = ok ? F.m[i][c0 + j] : R(0);
+                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
+                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
+            }
+        }
+        R iwd[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) iwd[i] = R(1) / F.wdep[i][r];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+            R x[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const R pi = first ? lv[i][k] : lv[i][k] + beta[i] * pv[i][k];
+                R wl, iwl;
+                lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
+                R inv_w = iwl * iwd[i];
+                if (F.whard[i]) inv_w /= wh[i][k];
+                if (ok) {
+                    F.p[i][c0 + j] = pi;
+                    acc[i] += pi * lv[i][k];
+                    acc[2 + i] += pi * pi;
+                }
+                x[i] = ok ? pi * inv_w : R(0);
+            }
+            a[k] = x[0];
+            b[k] = x[1];
+        }
+    }
     __device__ void flush(double *red) {
         block_accumulate<2>(acc, S->pl, red);
         block_accumulate<2>(acc + 2, S->pp, red);
@@ -238,6 +424,19 @@ struct EpiQNorm {
         const R q0 = F.wd[0][t] * a, q1 = F.wd[1][t] * b;
         acc[0] += q0 * q0;
         acc[1] += q1 * q1;
+    }
+    template <int K>
+    __device__ __forceinline__ void store_batch(int la, int, bool, int j0, int stride, int n, const R (&a)[K],
+                                                const R (&b)[K]) {
+        const size_t t0 = (size_t)la * sx;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            if (j >= n) continue;
+            const R q0 = F.wd[0][t0 + j] * a[k], q1 = F.wd[1][t0 + j] * b[k];
+            acc[0] += q0 * q0;
+            acc[1] += q1 * q1;
+        }
     }
     __device__ void flush(double *red) { block_accumulate<2>(acc, S->qq, red); }
 };
@@ -352,6 +551,8 @@ template <typename R>
 struct SolverLaunch {
     gj_rrcg *sv;
     OpView<R> v0, v1;
+    f512::View2<R> V2;
+    bool fast = false;
     FieldVecs<R> F;
     int P, C, L;
     size_t rsm, msm, csm;
@@ -361,6 +562,10 @@ struct SolverLaunch {
         const gj_op *o = sv->op[0];
         v0 = view_of<R>(sv->op[0]);
         v1 = view_of<R>(sv->op[1]);
+        if constexpr (std::is_same_v<R, float>) {
+            fast = o->fast && sv->op[1]->fast;
+            if (fast) V2 = f512::make_view2<R>(sv->op[0], sv->op[1]);
+        }
         const size_t cs = sizeof(cpx<R>);
         P = o->P_row; C = o->C_col; L = o->L_grp;
         rsm = row_smem(o->Nx, P, cs);
@@ -382,6 +587,16 @@ struct SolverLaunch {
     }
 
     void set_attributes() {
+        if constexpr (std::is_same_v<R, float>) if (fast) {
+            f512::set_row_fwd_attr<R, ProModel<R>>();
+            f512::set_row_fwd_attr<R, ProDirection<R>>();
+            f512::set_row_fwd_attr<R, LoadPair<R>>();
+            f512::set_row_inv_attr<R, EpiResidual<R>>();
+            f512::set_row_inv_attr<R, EpiGradient<R>>();
+            f512::set_row_inv_attr<R, EpiQNorm<R>>();
+            f512::set_col_attr<R>();
+            return;
+        }
         cudaFuncSetAttribute(k_row_fwd<R, ProModel<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
         cudaFuncSetAttribute(k_row_fwd<R, ProDirection<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
         cudaFuncSetAttribute(k_row_fwd<R, LoadPair<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
@@ -397,6 +612,19 @@ struct SolverLaunch {
     // Forward columns (Y = sum_r T^_r FFT_y(Z_r)) and inverse columns, both fields.
     void forward_columns(cudaStream_t st) {
         const gj_op *o = sv->op[0];
+        if constexpr (std::is_same_v<R, float>) if (fast) {
+            ProfilePair pp{};
+            if (sv->profile) {
+                pp = take_pair(sv);
+                cudaEventRecord(pp.a, st);
+            }
+            f512::col_fwd<R>(V2, o->col_grid, &sv->S->done, st);
+            if (sv->profile) {
+                cudaEventRecord(pp.b, st);
+                (sv->capturing ? sv->graph_pairs : sv->eager_pairs).push_back(pp);
+            }
+            return;
+        }
         const size_t cs = sizeof(cpx<R>);
         cudaMemsetAsync(v0.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
         cudaMemsetAsync(v1.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
@@ -417,6 +645,15 @@ struct SolverLaunch {
     void head(cudaStream_t st) {  // forward of (updated) m, residual, chi^2 scalars
         const gj_op *o = sv->op[0];
         const int *done = &sv->S->done;
+        if constexpr (std::is_same_v<R, float>) if (fast) {
+            ProModel<R> pm{F, sv->S, o->nx, o->ny};
+            f512::row_fwd<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
+            forward_columns(st);
+            EpiResidual<R> er{F, sv->S, o->sx};
+            f512::row_inv<R>(V2, 1, o->sy, o->sy, o->sx, 1, er, done, st);
+            k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
+            return;
+        }
         PairMap pc{o->nz * o->ny, 1};
         ProModel<R> pm{F, sv->S, o->nx, o->ny};
         k_row_fwd<R, ProModel<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pm, done);
@@ -430,6 +667,21 @@ struct SolverLaunch {
     void body(cudaStream_t st) {
         const gj_op *o = sv->op[0];
         const int *done = &sv->S->done;
+        if constexpr (std::is_same_v<R, float>) if (fast) {
+            LoadPair<R> lv{F.v[0], F.v[1], o->sx};
+            f512::row_fwd<R>(V2, 1, o->sy, o->sy, o->sx, 1, lv, done, st);
+            f512::col_adj<R>(V2, o->col_grid, done, st);
+            EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
+            f512::row_inv<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
+            ProDirection<R> pd{F, sv->S, o->nx, o->ny};
+            f512::row_fwd<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
+            forward_columns(st);
+            EpiQNorm<R> eq{F, sv->S, o->sx};
+            f512::row_inv<R>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
+            k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
+            head(st);
+            return;
+        }
         const int nt = (o->ncol + C - 1) / C;
         PairMap ps{o->sy, 1};
         PairMap pc{o->nz * o->ny, 1};
@@ -609,6 +861,11 @@ extern "C" gj_status gj_rrcg_report_get(gj_rrcg *sv, gj_rrcg_report *rep, gj_str
     rep->alpha[0] = h.alpha[0];
     rep->alpha[1] = h.alpha[1];
     rep->S_G = h.SG_last;
+    if (sv->op[0]->err) {
+        int e = 0;
+        GJ_CUDA(cudaMemcpy(&e, sv->op[0]->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e != 0 && rep->status == GJ_OK) rep->status = e;
+    }
     return GJ_OK;
 }
 

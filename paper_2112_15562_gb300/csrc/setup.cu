@@ -101,7 +101,8 @@ struct LoadTable {
 
 // Column pass of the setup: spec[r] = FFT_y of the row-pass output of layer r.
 template <typename Rout>
-__global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const double2 *Zs, cpx<Rout> *spec, int C) {
+__global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const double2 *Zs, cpx<Rout> *spec, int C,
+                                                  int transposed) {
     using Cx = double2;
     const int c0 = blockIdx.x * C;
     const int r = blockIdx.y;
@@ -121,7 +122,10 @@ __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const doubl
     cpx<Rout> *Sr = spec + (size_t)r * Ny * ncol;
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
         const int c = it % C, ky = it / C;
-        if (c0 + c < ncol) Sr[(size_t)ky * ncol + c0 + c] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
+        if (c0 + c < ncol) {
+            const size_t at = transposed ? (size_t)(c0 + c) * Ny + ky : (size_t)ky * ncol + c0 + c;
+            Sr[at] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
+        }
     }
 }
 
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const doubl
 // Host helpers
 
 bool plan_size(int N, FftPlanDev &plan) {
-    if (N < 1 || N > 4096) return false;
+    if (N < 1 || N > 2048) return false;
     int n = N, e = 0;
     while (n % 2 == 0) { n /= 2; ++e; }
     std::vector<int> rs(e / 3, 8);
@@ -178,6 +182,23 @@ void make_twiddles(int N, std::vector<double> &re, std::vector<double> &im) {
 }
 
 size_t elem_bytes(gj_precision p) { return p == GJ_FP64 ? sizeof(double) : sizeof(float); }
+
+bool fast_eligible(const gj_op *op) {
+    return op->prec == GJ_FP32_MIXED && op->Nx == 512 && op->Ny == 512 && op->nx <= 256 && op->ny <= 256 &&
+           op->sx <= 256 && op->sy <= 256;
+}
+
+// Largest number of warps that share one (field, kx) column when the persistent
+// column kernels split the (field, kx, layer) sequence into balanced segments.
+int fast_slots(int nfield, int nz, int grid_ctas) {
+    const long long T = (long long)nfield * 257 * nz;
+    const long long Wt = std::min((long long)grid_ctas * 8, T);
+    auto owner = [&](long long t) { return ((t + 1) * Wt + T - 1) / T - 1; };
+    long long mx = 1;
+    for (long long c = 0; c < (long long)nfield * 257; ++c)
+        mx = std::max(mx, owner(c * nz + nz - 1) - owner(c * nz) + 1);
+    return (int)mx;
+}
 
 int pick_row_pairs(int Nx, size_t cs) {
     int P = 16;
@@ -291,7 +312,7 @@ static gj_status build_spectra(gj_op *op, cudaStream_t st) {
     const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
     cudaFuncSetAttribute(k_col_spec<Rout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
     dim3 g((op->ncol + C - 1) / C, op->nz);
-    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C);
+    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C, op->fast ? 1 : 0);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(zw_d);
@@ -335,7 +356,7 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     if (!op) { set_error("gj_bttb_setup: host allocation failed"); return GJ_ERR_OOM; }
     if (!plan_size(Nx, op->px) || !plan_size(Ny, op->py)) {
         delete op;
-        set_error("gj_bttb_setup: padded size unsupported (must be <= 4096 with prime factors <= 17)");
+        set_error("gj_bttb_setup: padded size unsupported (must be <= 2048 with prime factors <= 17)");
         return GJ_ERR_UNSUPPORTED;
     }
     op->sx = G.sx; op->sy = G.sy; op->nx = G.nx; op->ny = G.ny; op->nz = G.nz;
@@ -349,6 +370,14 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     op->P_row = pick_row_pairs(Nx, cs);
     op->C_col = pick_col_tile(Ny, cs, 3);
     op->L_grp = 4;
+    op->fast = fast_eligible(op);
+    if (op->fast) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        op->col_grid = std::max(1, sms);
+        op->slots = std::max(fast_slots(1, G.nz, op->col_grid), fast_slots(2, G.nz, op->col_grid));
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     gj_status rc;
     cudaError_t e;
@@ -358,7 +387,7 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     if ((e = cudaMalloc(&op->spec, op->spec_bytes)) != cudaSuccess) { rc = cuda_fail(e, "spectra"); goto fail; }
     rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
     if (rc != GJ_OK) goto fail;
-    {
+    if (!op->fast) {
         const size_t zb = (size_t)G.nz * G.ny * op->ncol * cs;
         const size_t yb = (size_t)Ny * op->ncol * cs;
         const size_t wb = (size_t)std::max(G.sy, 1) * op->ncol * cs;
@@ -366,6 +395,23 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
         if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->Y, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+    } else {
+        // transposed intermediates [r][kx][256], partials [kx][slots][512], counters
+        const size_t zb = (size_t)G.nz * 257 * 256 * cs;
+        const size_t wb = (size_t)257 * 256 * cs;
+        const size_t pb = (size_t)257 * op->slots * 512 * cs;
+        const size_t yb = pb + 257 * sizeof(int) + 64;
+        op->ws_bytes = zb + wb + yb;
+        if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMalloc(&op->Y, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        // rows beyond the prisms / stations must read as zero; counters start at zero
+        if ((e = cudaMemset(op->Z, 0, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMemset(op->W, 0, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMemset(op->Y, 0, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        op->P = op->Y;
+        op->cnt = reinterpret_cast<int *>(static_cast<char *>(op->Y) + pb);
+        op->err = op->cnt + 257 + 8;
     }
     *out = op;
     return GJ_OK;
@@ -382,6 +428,7 @@ extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {
     info->field = op->field; info->precision = op->prec;
     info->spectrum_bytes = (int64_t)op->spec_bytes;
     info->workspace_bytes = (int64_t)op->ws_bytes;
+    info->fast_path = op->fast ? 1 : 0;
     return GJ_OK;
 }
 

@@ -30,8 +30,9 @@ def run_oracle(g, A, dob, sig, wdep, P, m0=None):
                       dob, sig, m0, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)], P)
 
 
-def run_gpu(gj, w, g, dob, sig, wdep, prec, kw, m0=None, graph=None):
-    ops = [gj.bttb_setup(g, "gravity", precision=prec), gj.bttb_setup(g, "magnetic", w.mag, precision=prec)]
+def run_gpu(gj, w, g, dob, sig, wdep, prec, kw, m0=None, graph=None, npad=(0, 0)):
+    ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
+           gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
     m = [to_dev(np.zeros(g.n) if m0 is None else m0[i], prec) for i in range(2)]
     args = ([to_dev(x, prec) for x in dob], [to_dev(x, prec) for x in sig], [to_dev(x, prec) for x in wdep], m)
     P = gj.solver_params(**kw)
@@ -126,3 +127,29 @@ def test_stepwise_graph_and_eager_match_one_shot(small, graph):
     assert r1["iterations"] == r2["iterations"] == 12
     for i in range(2):
         assert rel(m2[i], m1[i]) <= 1e-12
+
+
+def test_joint_fp32_on_the_512_kernels(small):
+    """The same solve with 512 x 512 embeddings, served by the specialised kernels."""
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(KW))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", KW, npad=(512, 512))
+    assert rep["iterations"] == 50
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
+    for k in (0, 1, 10, 49):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-3)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_fast_graph_and_eager_agree(small, graph):
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    kw = dict(KW, kmax=10)
+    m1, r1 = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=(512, 512))
+    m2, r2 = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, graph=graph, npad=(512, 512))
+    for i in range(2):
+        # dot products are summed with floating-point atomics: agreement to rounding
+        assert rel(m2[i], m1[i]) <= 1e-5
