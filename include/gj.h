@@ -138,6 +138,30 @@ gj_status gj_gramian_value_grad(int64_t n, gj_precision precision,
                                 const void *m1, const void *m2, double *S,
                                 void *l1, void *l2, gj_stream_t stream);
 
+/*
+ * gj_gramian_value_grad_noalloc - the same outputs as gj_gramian_value_grad,
+ * for callers that must not allocate device memory: code running under a CUDA
+ * stream capture that may not create allocations, hosts whose device memory is
+ * owned by another allocator (a framework's caching pool, a fixed arena), or
+ * real-time loops that forbid allocation.  (The paper has no counterpart; this
+ * is an interface for such callers.)
+ *
+ * The call allocates nothing: no cudaMalloc, cudaMallocAsync or cudaFree.  Its
+ * reduction scratch is a fixed 131,096-byte device array inside the library,
+ * which every GPU that loads the library holds until the process exits.  The
+ * first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  Limit: n <= 16,777,216; larger n returns GJ_ERR_ARG
+ * (use gj_gramian_value_grad).  All calls on a device share the array, which
+ * keeps the last call's contents; every slot a call reads is written earlier
+ * in the same call, so nothing needs clearing.  Calls that overlap on the GPU
+ * (other streams, other host threads) race on the array: serialise them.
+ * Arguments, outputs and precisions are those of gj_gramian_value_grad.
+ */
+gj_status gj_gramian_value_grad_noalloc(int64_t n, gj_precision precision,
+                                        const void *m1, const void *m2, double *S,
+                                        void *l1, void *l2, gj_stream_t stream);
+
 /* Solver options (Eq. RRCG:1-8; Secs. 2.5, 2.6, 2.8). Index 0 = gravity, 1 = magnetic. */
 enum { GJ_SCALARS_AUTO = 0, GJ_SCALARS_JOINT = 1, GJ_SCALARS_PER_FIELD = 2 };
 

@@ -76,6 +76,7 @@ def load() -> ct.CDLL:
         "gj_g_forward": (i32, [vp, vp, vp, vp]),
         "gj_g_adjoint": (i32, [vp, vp, vp, vp]),
         "gj_gramian_value_grad": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),
+        "gj_gramian_value_grad_noalloc": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),
         "gj_rrcg_joint_solve": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp, vp,
                                       ct.POINTER(RRCGReport), vp]),
         "gj_rrcg_create": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp, vp, vp, pp]),

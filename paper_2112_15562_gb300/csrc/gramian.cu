@@ -1,4 +1,7 @@
 // The Gramian coupling term (Eq. Gramian) and its ascent directions (RRCG:2-3).
+#include <mutex>
+#include <string>
+
 #include "view.cuh"
 
 namespace gj {
@@ -89,4 +92,83 @@ extern "C" gj_status gj_gramian_value_grad(int64_t n, gj_precision prec, const v
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     return prec == GJ_FP64 ? gj::gramian_launch<double>(n, m1, m2, S, l1, l2, st)
                            : gj::gramian_launch<float>(n, m1, m2, S, l1, l2, st);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  The reduction scratch lives in a file-scope device
+// array (every GPU that loads the library keeps it until exit) instead of a
+// per-call cudaMallocAsync.  Host code never passes the array's name to a kernel
+// (on the host it is only a stand-in symbol): its device address is looked up once
+// per device with cudaGetSymbolAddress while that device is current.
+
+namespace gj {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 4096;             // partial sums per call
+constexpr int64_t kNoAllocChunk = 4096;             // elements per block
+constexpr int64_t kNoAllocMaxN = (int64_t)kNoAllocMaxBlocks * kNoAllocChunk;  // 16,777,216
+constexpr int kNoAllocDoubles = 3 * kNoAllocMaxBlocks + 3 + kNoAllocMaxBlocks;  // 131,096 bytes
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
+
+gj_status noalloc_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "gj_gramian_value_grad_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("gj_gramian_value_grad_noalloc: device index above 63");
+        return GJ_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "gj_gramian_value_grad_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return GJ_OK;
+}
+
+template <typename R>
+gj_status gramian_launch_noalloc(int64_t n, const void *m1, const void *m2, double *S, void *l1, void *l2,
+                                 cudaStream_t st) {
+    double *scratch = nullptr;
+    gj_status rc = noalloc_scratch(&scratch);
+    if (rc != GJ_OK) return rc;
+    const int nb = (int)((n + kNoAllocChunk - 1) / kNoAllocChunk);
+    double *part = scratch;                                  // 3 per block
+    double *sums = scratch + 3 * kNoAllocMaxBlocks;          // 3
+    double *part2 = sums + 3;                                // 1 per block
+    // every slot that is read is written earlier in the same call: nothing needs clearing
+    k_gram_dots<R><<<nb, 256, 0, st>>>(n, (const R *)m1, (const R *)m2, part);
+    k_gram_finish<<<1, 256, 0, st>>>(nb, part, sums);
+    k_gram_dirs<R><<<nb, 256, 0, st>>>(n, (const R *)m1, (const R *)m2, sums, (R *)l1, (R *)l2, part2);
+    k_gram_value<<<1, 256, 0, st>>>(nb, part2, sums, S);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GJ_OK : cuda_fail(e, "gramian (no allocation) launch");
+}
+
+}  // namespace
+}  // namespace gj
+
+extern "C" gj_status gj_gramian_value_grad_noalloc(int64_t n, gj_precision prec, const void *m1, const void *m2,
+                                                   double *S, void *l1, void *l2, gj_stream_t stream) {
+    if (n > gj::kNoAllocMaxN) {
+        gj::set_error("gj_gramian_value_grad_noalloc: n = " + std::to_string(n) +
+                      " exceeds the allocation-free limit of 16777216 elements (use gj_gramian_value_grad)");
+        return GJ_ERR_ARG;
+    }
+    if (n < 1 || !m1 || !m2 || !S) { gj::set_error("gj_gramian_value_grad_noalloc: bad argument"); return GJ_ERR_ARG; }
+    if (prec != GJ_FP64 && prec != GJ_FP32_MIXED) {
+        gj::set_error("gj_gramian_value_grad_noalloc: bad precision");
+        return GJ_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return prec == GJ_FP64 ? gj::gramian_launch_noalloc<double>(n, m1, m2, S, l1, l2, st)
+                           : gj::gramian_launch_noalloc<float>(n, m1, m2, S, l1, l2, st);
 }
