@@ -26,6 +26,7 @@ struct OpView {
     cpx<R> *Z;           // [nz*ny][ncol]  row-pass output / adjoint column output
     cpx<R> *Y;           // [Ny][ncol]     summed spectrum / residual spectrum
     cpx<R> *W;           // [max(sy, ...)][ncol]  inverse-column output / residual rows
+    cpx<R> *V;           // fast path: residual-row spectra [ncol][256] (unused otherwise)
 };
 
 // How real lines are paired into complex transforms.

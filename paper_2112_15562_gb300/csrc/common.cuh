@@ -50,13 +50,31 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 }
 
 // Adds per-thread partials acc[0..K) into out[0..K) (one double atomic per
-// block per entry).  All threads must call it.
+// block per entry).  All K sums share one pass: warp shuffles, one barrier, and
+// the first warp finishes.  `scratch` holds at least 32 doubles (K * warps <= 32).
+// All threads must call it.
 template <int K, typename A>
 __device__ __forceinline__ void block_accumulate(const A *acc, double *out, double *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    double v[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double s = block_sum((double)acc[k], scratch);
-        if (threadIdx.x == 0 && out) atomicAdd(out + k, s);
+        v[k] = (double)acc[k];
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();  // scratch may still be in use by an earlier call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[k * nw + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? scratch[k * nw + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0 && out) atomicAdd(out + k, t);
+        }
     }
 }
 

@@ -256,36 +256,83 @@ struct View2 {  // the two fields of a launch (field 1 unused in single-field la
 
 // ---------------------------------------------------------------------------
 // Row pass (x direction), real lines -> half spectra in the transposed layout.
-// CTA: WARPS warps x 2 complex transforms = 16 transforms.  Joint mode: transform
-// f packs line (base + f) of field 0 (real) and field 1 (imaginary); single mode:
-// lines (base + 2f, base + 2f + 1) of field 0.  lpl = lines per layer (ny or sy).
-template <typename R, class Pro>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_row_fwd512(View2<R> V, int joint, int nlines, int lpl, int n_in,
-                                                           int out_is_W, Pro pro, const int *done) {
+// A CTA of NW warps runs FPW complex transforms per warp (FFTS = NW * FPW per CTA).
+// Joint mode: transform f packs line (base + f) of field 0 (real part) and field 1
+// (imaginary part); single mode: lines (base + 2f, base + 2f + 1) of field 0.
+// lpl = lines per layer (ny for model lines, sy for data lines).
+
+__device__ __forceinline__ void pair_lines(int joint, int base, int f, int nlines, int &la, int &lb, bool &ha,
+                                           bool &hb) {
+    if (joint) { la = lb = base + f; ha = hb = la < nlines; }
+    else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
+}
+
+// Splits the staged spectra of FFTS transforms into the two real half spectra and
+// writes them to out[r][kx][iy] (the transposed layout), iy fastest.
+template <typename R, int FFTS>
+__device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const View2<R> &V, int joint, int base,
+                                                   int nlines, int lpl, int out_sel) {
     using C = cpx<R>;
+    static_assert((FFTS & (FFTS - 1)) == 0, "FFTS must be a power of two");
+    // blockDim is a multiple of FFTS, so this thread always serves transform f
+    const int f = threadIdx.x % FFTS;
+    int la, lb;
+    bool ha, hb;
+    pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+    const int fb = joint ? 1 : 0;
+    const int ra = ha ? la / lpl : 0, rb = hb ? lb / lpl : 0;
+    C *oa = (out_sel == 0 ? V.op[0].Z : (out_sel == 1 ? V.op[0].W : V.op[0].V)) + (size_t)ra * NC * H + (la - ra * lpl);
+    C *ob = (out_sel == 0 ? V.op[fb].Z : (out_sel == 1 ? V.op[fb].W : V.op[fb].V)) + (size_t)rb * NC * H + (lb - rb * lpl);
+    const C *row = tile + f * (N + 1);
+    const int kstep = blockDim.x / FFTS;
+    for (int kx = threadIdx.x / FFTS; kx < NC; kx += kstep) {
+        const C zk = row[kx];
+        const C zm = row[(N - kx) & (N - 1)];
+        if (ha) oa[kx * H] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (hb) ob[kx * H] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    }
+}
+
+// Real input a + i b held as a[i], b[i] for elements lane + 32 i: redistribute
+// through the warp tile and run the forward transform.  Result in v (lane layout).
+template <typename R>
+__device__ __forceinline__ void fwd512_from_lines(const R (&a)[8], const R (&b)[8], cpx<R> *buf, const LaneTw<R> &tw,
+                                                  cpx<R> (&v)[16]) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, l = lane & 15;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = buf[l + 16 * j];
+    fwd512<R>(v, buf, tw);
+}
+
+template <typename R, class Pro, int NW, int FPW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint, int nlines, int lpl, int n_in,
+                                                           int out_sel, Pro pro, const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW * FPW;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);         // [16][N + 1]
-    C *xb = tile + 16 * (N + 1);                          // per warp 512
-    C *tws = xb + WARPS * N;                              // W512 table
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [FFTS][N + 1]
+    C *xb = tile + FFTS * (N + 1);              // per warp 512
+    C *tws = xb + NW * N;                       // W512 table
     __shared__ double red[32];
-    const OpView<R> &op0 = V.op[0];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = op0.twx[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
     pro.init();
     __syncthreads();
     LaneTw<R> tw;
     tw.load(tws);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
-    const int per_tile = joint ? 16 : 32;
-    const int base = blockIdx.x * per_tile;
+    const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
     C *buf = xb + warp * N;
-    for (int s = 0; s < 2; ++s) {
-        const int f = warp * 2 + s;
+    for (int s = 0; s < FPW; ++s) {
+        const int f = warp * FPW + s;
         int la, lb;
         bool ha, hb;
-        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
-        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
-        // all lanes fetch elements lane + 32 i (contiguous), then redistribute
+        pair_lines(joint, base, f, nlines, la, lb, ha, hb);
         R a[8], b[8];
         if (ha) {
             pro.template fetch_batch<8>(la, lb, hb, lane, 32, n_in, a, b);
@@ -293,128 +340,159 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_row_fwd512(View2<R> V, int jo
 #pragma unroll
             for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
         }
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
-        __syncwarp();
         C v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = buf[l + 16 * j];
-        fwd512<R>(v, buf, tw);
-        // natural-order spectrum of this transform into the staging tile
+        fwd512_from_lines<R>(a, b, buf, tw, v);
         const int lam = 2 * l + h;
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + lam + 32 * k1] = v[k1];
     }
     __syncthreads();
-    // split into the two real half spectra and write Zt[r][kx][iy]
-    for (int it = threadIdx.x; it < NC * 16; it += blockDim.x) {
-        const int f = it & 15, kx = it >> 4;
-        const C zk = tile[f * (N + 1) + kx];
-        const C zm = tile[f * (N + 1) + ((N - kx) & (N - 1))];
-        const C A = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-        const C B = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-        int la, lb;
-        bool ha, hb;
-        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
-        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
-        if (ha) {
-            const int r = la / lpl, iy = la - r * lpl;
-            C *o = out_is_W ? V.op[0].W : V.op[0].Z;
-            o[((size_t)r * NC + kx) * H + iy] = A;
-        }
-        if (hb) {
-            const int fb = joint ? 1 : 0;
-            const int r = lb / lpl, iy = lb - r * lpl;
-            C *o = out_is_W ? V.op[fb].W : V.op[fb].Z;
-            o[((size_t)r * NC + kx) * H + iy] = B;
-        }
-    }
+    write_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, out_sel);
     pro.flush(red);
 }
 
-// ---------------------------------------------------------------------------
-// Inverse row pass: half spectra in[r][kx][iy] -> real lines, cropped to n_out.
-template <typename R, class Epi>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_row_inv512(View2<R> V, int joint, int nlines, int lpl, int n_out,
-                                                           int in_is_W, Epi epi, const int *done) {
+// Stages the half spectra of the CTA's lines: source column s < 2 FFTS holds
+// (joint) field s / FFTS, line base + s % FFTS, or (single) line base + s.
+template <typename R, int FFTS>
+__device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> &V, int joint, int base, int nlines,
+                                                   int lpl, int in_sel) {
     using C = cpx<R>;
+    constexpr int SRC = 2 * FFTS, P = SRC + 1;
+    const int s = threadIdx.x % SRC;
+    const int fld = joint ? (s / FFTS) : 0;
+    const int line = joint ? base + (s % FFTS) : base + s;
+    const bool ok = line < nlines;
+    const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
+    const C *src = in_sel == 0 ? V.op[fld].Z : (in_sel == 1 ? V.op[fld].W : V.op[fld].V);
+    const C *in = src + (size_t)r * NC * H + iy;
+    const int kx0 = threadIdx.x / SRC, kstep = blockDim.x / SRC;
+    for (int kb = kx0; kb < NC; kb += 8 * kstep) {
+        C val[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kx = kb + u * kstep;
+            val[u] = (ok && kx < NC) ? in[(size_t)kx * H] : czero<C>();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kx = kb + u * kstep;
+            if (kx < NC) tile[kx * P + s] = val[u];
+        }
+    }
+}
+
+// Gathers transform f (sources sa, sb: Hermitian-extended A + i B) in the lane
+// layout and runs the inverse transform; returns y[lane + 32 i] in a[i] + i b[i].
+template <typename R, int FFTS>
+__device__ __forceinline__ void inv512_to_lines(const cpx<R> *tile, int sa, int sb, cpx<R> *buf, const LaneTw<R> &tw,
+                                                R (&a)[8], R (&b)[8]) {
+    using C = cpx<R>;
+    constexpr int P = 2 * FFTS + 1;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    C v[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+        const int k = lam + 32 * k1;
+        const bool lo = k <= H;
+        const int kk = lo ? k : N - k;
+        C A = tile[kk * P + sa], B = tile[kk * P + sb];
+        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+        v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+    }
+    C out[8];
+    inv512<R>(v, buf, tw, out);
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const C y = buf[lane + 32 * i];
+        a[i] = y.x;
+        b[i] = y.y;
+    }
+}
+
+// Inverse row pass: half spectra in[r][kx][iy] -> real lines, cropped to n_out,
+// through the epilogue functor.
+template <typename R, class Epi, int NW, int FPW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint, int nlines, int lpl, int n_out,
+                                                           int in_sel, Epi epi, const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW * FPW;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][33]
-    C *xb = tile + NC * 33;
-    C *tws = xb + WARPS * N;
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 FFTS + 1]
+    C *xb = tile + NC * (2 * FFTS + 1);
+    C *tws = xb + NW * N;
     __shared__ double red[32];
     for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
     epi.init();
-    const int per_tile = joint ? 16 : 32;
-    const int base = blockIdx.x * per_tile;
-    // stage: source column s < 32 -> (field, line); joint: s = 16*field + f, line base + f
-    {
-        // this thread's source column s is fixed; issue 8 loads before storing any
-        const int s = threadIdx.x & 31;
-        const int fld = joint ? (s >> 4) : 0;
-        const int line = joint ? base + (s & 15) : base + s;
-        const bool ok = line < nlines;
-        const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
-        const C *in = (in_is_W ? V.op[fld].W : V.op[fld].Z) + (size_t)r * NC * H + iy;
-        const int kx0 = threadIdx.x >> 5, kstep = blockDim.x >> 5;
-        for (int kb = kx0; kb < NC; kb += 8 * kstep) {
-            C val[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int kx = kb + u * kstep;
-                val[u] = (ok && kx < NC) ? in[(size_t)kx * H] : czero<C>();
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int kx = kb + u * kstep;
-                if (kx < NC) tile[kx * 33 + s] = val[u];
-            }
-        }
+    const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
+    stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load(tws);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *buf = xb + warp * N;
+    for (int s2 = 0; s2 < FPW; ++s2) {
+        const int f = warp * FPW + s2;
+        const int sa = joint ? f : 2 * f;
+        const int sb = joint ? FFTS + f : 2 * f + 1;
+        R a[8], b[8];
+        inv512_to_lines<R, FFTS>(tile, sa, sb, buf, tw, a, b);
+        int la, lb;
+        bool ha, hb;
+        pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+        if (ha) epi.template store_batch<8>(la, lb, hb, lane, 32, n_out, a, b);
     }
+    epi.flush(red);
+}
+
+// Fused data-line pass of the solver: for station row jy of both fields, inverse
+// row transform of W (the cropped forward product), the residual epilogue
+// (r~ = W_d (A m - d), v = W_d r~, Phi partials), then the forward row transform
+// of v written to V[kx][jy] for the adjoint's column pass.
+template <typename R, class Epi, int NW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nlines, int n_out, Epi epi,
+                                                             const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW;  // one joint transform per warp
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 NW + 1], later [NW][N + 1]
+    C *xb = tile + (NC * (2 * FFTS + 1) > FFTS * (N + 1) ? NC * (2 * FFTS + 1) : FFTS * (N + 1));
+    C *tws = xb + NW * N;
+    __shared__ double red[32];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
+    epi.init();
+    const int base = blockIdx.x * FFTS;
+    stage_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 1);
     __syncthreads();
     LaneTw<R> tw;
     tw.load(tws);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
-    const int lam = 2 * l + h;
     C *buf = xb + warp * N;
-    for (int s2 = 0; s2 < 2; ++s2) {
-        const int f = warp * 2 + s2;
-        const int sa = joint ? f : 2 * f;
-        const int sb = joint ? 16 + f : 2 * f + 1;
-        C v[16];
+    const int f = warp;
+    R a[8], b[8];
+    inv512_to_lines<R, FFTS>(tile, f, FFTS + f, buf, tw, a, b);
+    const int line = base + f;
+    const bool ok = line < nlines;
+    if (ok) {
+        epi.template resid_batch<8>(line, lane, 32, n_out, a, b);  // a, b <- v of both fields
+    } else {
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) {
-            const int k = lam + 32 * k1;
-            const bool lo = k <= H;
-            const int kk = lo ? k : N - k;
-            C A = tile[kk * 33 + sa], B = tile[kk * 33 + sb];
-            if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
-            v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
-        }
-        C out[8];
-        inv512<R>(v, buf, tw, out);
-        int la, lb;
-        bool ha, hb;
-        if (joint) { la = lb = base + f; ha = hb = la < nlines; }
-        else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
-        // natural order through the warp tile, then contiguous batches per lane
-        __syncwarp();
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
-        __syncwarp();
-        if (ha) {
-            R a[8], b[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const C y = buf[lane + 32 * i];
-                a[i] = y.x;
-                b[i] = y.y;
-            }
-            epi.template store_batch<8>(la, lb, hb, lane, 32, n_out, a, b);
-        }
+        for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
     }
+    C v[16];
+    fwd512_from_lines<R>(a, b, buf, tw, v);
+    __syncthreads();  // every warp is done reading the staged input
+    const int lam = 2 * l + h;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + lam + 32 * k1] = v[k1];
+    __syncthreads();
+    write_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 2);
     epi.flush(red);
 }
 
@@ -587,7 +665,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
         const OpView<R> &op = V.op[fld];
         if (col != cur_col) {
             // V^ = FFT512 of the residual column (rows >= sy are zero)
-            const C *Wc = op.W + (size_t)kx * H;
+            const C *Wc = op.V + (size_t)kx * H;
 #pragma unroll
             for (int j = 0; j < 16; ++j) vh[j] = Wc[l + 16 * j];
             fwd512<R>(vh, xbuf, tw);
@@ -615,8 +693,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
 }
 
 // shared-memory bytes of each kernel
-template <typename R> inline size_t smem_row_fwd() { return (size_t)(16 * (N + 1) + WARPS * N + N) * sizeof(cpx<R>); }
-template <typename R> inline size_t smem_row_inv() { return (size_t)(NC * 33 + WARPS * N + N) * sizeof(cpx<R>); }
+template <typename R, int NW, int FPW> inline size_t smem_row_fwd() {
+    return (size_t)(NW * FPW * (N + 1) + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW, int FPW> inline size_t smem_row_inv() {
+    return (size_t)(NC * (2 * NW * FPW + 1) + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW> inline size_t smem_row_resid() {
+    const size_t t = (size_t)NC * (2 * NW + 1) > (size_t)NW * (N + 1) ? (size_t)NC * (2 * NW + 1) : (size_t)NW * (N + 1);
+    return (t + NW * N + N) * sizeof(cpx<R>);
+}
 template <typename R> inline size_t smem_col_fwd() {
     return (size_t)WARPS * (STAGES * (H + N) + N) * sizeof(cpx<R>) + N * sizeof(cpx<R>);
 }

@@ -21,13 +21,23 @@ inline View2<R> make_view2(const gj_op *a, const gj_op *b) {
     return V;
 }
 
-template <typename R, class Pro>
+// row-pass shapes: cell lines use 8 warps x 2 transforms, data lines 4 warps x 1
+constexpr int kCellNW = 8, kCellFPW = 2, kDataNW = 4, kDataFPW = 1;
+
+template <typename R, class Pro, int NW, int FPW>
 inline void set_row_fwd_attr() {
-    cudaFuncSetAttribute(k_row_fwd512<R, Pro>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row_fwd<R>());
+    cudaFuncSetAttribute(k_row_fwd512<R, Pro, NW, FPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_row_fwd<R, NW, FPW>());
 }
-template <typename R, class Epi>
+template <typename R, class Epi, int NW, int FPW>
 inline void set_row_inv_attr() {
-    cudaFuncSetAttribute(k_row_inv512<R, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row_inv<R>());
+    cudaFuncSetAttribute(k_row_inv512<R, Epi, NW, FPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_row_inv<R, NW, FPW>());
+}
+template <typename R, class Epi, int NW>
+inline void set_row_resid_attr() {
+    cudaFuncSetAttribute(k_row_resid512<R, Epi, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_row_resid<R, NW>());
 }
 template <typename R>
 inline void set_col_attr() {
@@ -35,20 +45,27 @@ inline void set_col_attr() {
     cudaFuncSetAttribute(k_col_adj512<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col_adj<R>());
 }
 
-template <typename R, class Pro>
-inline void row_fwd(const View2<R> &V, int joint, int nlines, int lpl, int n_in, int out_is_W, const Pro &pro,
+// out_sel / in_sel: 0 = Z, 1 = W, 2 = V
+template <typename R, int NW, int FPW, class Pro>
+inline void row_fwd(const View2<R> &V, int joint, int nlines, int lpl, int n_in, int out_sel, const Pro &pro,
                     const int *done, cudaStream_t st) {
-    const int per = joint ? 16 : 32;
-    k_row_fwd512<R, Pro><<<(nlines + per - 1) / per, WARPS * 32, smem_row_fwd<R>(), st>>>(V, joint, nlines, lpl, n_in,
-                                                                                         out_is_W, pro, done);
+    const int per = (joint ? 1 : 2) * NW * FPW;
+    k_row_fwd512<R, Pro, NW, FPW><<<(nlines + per - 1) / per, NW * 32, smem_row_fwd<R, NW, FPW>(), st>>>(
+        V, joint, nlines, lpl, n_in, out_sel, pro, done);
 }
 
-template <typename R, class Epi>
-inline void row_inv(const View2<R> &V, int joint, int nlines, int lpl, int n_out, int in_is_W, const Epi &epi,
+template <typename R, int NW, int FPW, class Epi>
+inline void row_inv(const View2<R> &V, int joint, int nlines, int lpl, int n_out, int in_sel, const Epi &epi,
                     const int *done, cudaStream_t st) {
-    const int per = joint ? 16 : 32;
-    k_row_inv512<R, Epi><<<(nlines + per - 1) / per, WARPS * 32, smem_row_inv<R>(), st>>>(V, joint, nlines, lpl, n_out,
-                                                                                         in_is_W, epi, done);
+    const int per = (joint ? 1 : 2) * NW * FPW;
+    k_row_inv512<R, Epi, NW, FPW><<<(nlines + per - 1) / per, NW * 32, smem_row_inv<R, NW, FPW>(), st>>>(
+        V, joint, nlines, lpl, n_out, in_sel, epi, done);
+}
+
+template <typename R, int NW, class Epi>
+inline void row_resid(const View2<R> &V, int nlines, int n_out, const Epi &epi, const int *done, cudaStream_t st) {
+    k_row_resid512<R, Epi, NW><<<(nlines + NW - 1) / NW, NW * 32, smem_row_resid<R, NW>(), st>>>(V, nlines, n_out, epi,
+                                                                                                 done);
 }
 
 template <typename R>

@@ -22,7 +22,7 @@ struct gj_op {
     // device memory (op precision unless noted)
     void *twx = nullptr, *twy = nullptr;  // twiddles W_N^k
     void *spec = nullptr;                 // [nz][Ny][ncol] complex
-    void *Z = nullptr, *Y = nullptr, *W = nullptr;
+    void *Z = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
     size_t spec_bytes = 0, ws_bytes = 0;
     // launch shapes
     int P_row = 8, C_col = 8, L_grp = 4;

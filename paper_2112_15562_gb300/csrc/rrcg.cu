@@ -15,6 +15,7 @@
 //   scalars:  chi^2 flags, alpha freeze/decay, stop flag
 // The first forward of m_0 and its scalars run once when the solver is created.
 #include <math.h>
+#include <stddef.h>
 
 #include <algorithm>
 #include <new>
@@ -56,6 +57,7 @@ struct FieldVecs {
     const R *dobs[2];
     const R *mapr[2];      // may be null
     const R *wdep[2];      // nz values
+    const R *iwdep[2];     // 1 / wdep, nz values
     const R *whard[2];     // may be null
 };
 
@@ -86,6 +88,18 @@ __device__ __forceinline__ void lp_factors(int p, R d, R eps2, R &wl, R &inv_wl)
     } else {
         wl = R(1);
         inv_wl = R(1);
+    }
+}
+// FP32: two reciprocal square roots, u = q^-1/2, q^1/4 = u^-1/2, q^-1/4 = u q^1/4
+template <>
+__device__ __forceinline__ void lp_factors<float>(int p, float d, float eps2, float &wl, float &inv_wl) {
+    if (p == 1) {
+        const float u = rsqrtf(d * d + eps2);
+        inv_wl = rsqrtf(u);
+        wl = u * inv_wl;
+    } else {
+        wl = 1.0f;
+        inv_wl = 1.0f;
     }
 }
 
@@ -150,7 +164,7 @@ struct ProModel {
         if (upd) {
             R iwd[2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) iwd[i] = R(1) / F.wdep[i][r];
+            for (int i = 0; i < 2; ++i) iwd[i] = F.iwdep[i][r];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = j0 + k * stride;
@@ -197,6 +211,35 @@ struct EpiResidual {
             const R rt = w * (y[i] - F.dobs[i][t]);
             acc[i] += rt * rt;
             F.v[i][t] = w * rt;
+        }
+    }
+    // fused form: y in a, b on entry; v = W_d r~ of both fields in a, b on return
+    template <int K>
+    __device__ __forceinline__ void resid_batch(int la, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+        const size_t t0 = (size_t)la * sx;
+        R w[2][K], d[2][K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                w[i][k] = ok ? F.wd[i][t0 + j] : R(0);
+                d[i][k] = ok ? F.dobs[i][t0 + j] : R(0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k * stride;
+            const bool ok = j < n;
+            const R r0 = w[0][k] * (a[k] - d[0][k]);
+            const R r1 = w[1][k] * (b[k] - d[1][k]);
+            if (ok) {
+                acc[0] += r0 * r0;
+                acc[1] += r1 * r1;
+            }
+            a[k] = ok ? w[0][k] * r0 : R(0);
+            b[k] = ok ? w[1][k] * r1 : R(0);
         }
     }
     template <int K>
@@ -302,7 +345,7 @@ struct EpiGradient {
         }
         R wd[2], iwd[2];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) { wd[i] = F.wdep[i][r]; iwd[i] = R(1) / wd[i]; }
+        for (int i = 0; i < 2; ++i) { wd[i] = F.wdep[i][r]; iwd[i] = F.iwdep[i][r]; }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -381,7 +424,7 @@ struct ProDirection {
         }
         R iwd[2];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) iwd[i] = R(1) / F.wdep[i][r];
+        for (int i = 0; i < 2; ++i) iwd[i] = F.iwdep[i][r];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -406,8 +449,9 @@ struct ProDirection {
         }
     }
     __device__ void flush(double *red) {
-        block_accumulate<2>(acc, S->pl, red);
-        block_accumulate<2>(acc + 2, S->pp, red);
+        // pl and pp are adjacent in SolverDev: one pass adds all four sums
+        static_assert(offsetof(SolverDev, pp) == offsetof(SolverDev, pl) + 2 * sizeof(double), "layout");
+        block_accumulate<4>(acc, S->pl, red);
     }
 };
 
@@ -582,19 +626,20 @@ struct SolverLaunch {
             F.dobs[i] = static_cast<const R *>(sv->dobs[i]);
             F.mapr[i] = static_cast<const R *>(sv->mapr[i]);
             F.wdep[i] = static_cast<const R *>(sv->wdep[i]);
+            F.iwdep[i] = b + (size_t)4 * n + (size_t)4 * s + (size_t)i * o->nz;
             F.whard[i] = static_cast<const R *>(sv->whard[i]);
         }
     }
 
     void set_attributes() {
         if constexpr (std::is_same_v<R, float>) if (fast) {
-            f512::set_row_fwd_attr<R, ProModel<R>>();
-            f512::set_row_fwd_attr<R, ProDirection<R>>();
-            f512::set_row_fwd_attr<R, LoadPair<R>>();
-            f512::set_row_inv_attr<R, EpiResidual<R>>();
-            f512::set_row_inv_attr<R, EpiGradient<R>>();
-            f512::set_row_inv_attr<R, EpiQNorm<R>>();
-            f512::set_col_attr<R>();
+            using namespace f512;
+            set_row_fwd_attr<R, ProModel<R>, kCellNW, kCellFPW>();
+            set_row_fwd_attr<R, ProDirection<R>, kCellNW, kCellFPW>();
+            set_row_resid_attr<R, EpiResidual<R>, kDataNW>();
+            set_row_inv_attr<R, EpiGradient<R>, kCellNW, kCellFPW>();
+            set_row_inv_attr<R, EpiQNorm<R>, kDataNW, kDataFPW>();
+            set_col_attr<R>();
             return;
         }
         cudaFuncSetAttribute(k_row_fwd<R, ProModel<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
@@ -647,10 +692,12 @@ struct SolverLaunch {
         const int *done = &sv->S->done;
         if constexpr (std::is_same_v<R, float>) if (fast) {
             ProModel<R> pm{F, sv->S, o->nx, o->ny};
-            f512::row_fwd<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
+            using namespace f512;
+            row_fwd<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
             forward_columns(st);
+            // residual, Phi and the residual rows' spectra for the adjoint, in one pass
             EpiResidual<R> er{F, sv->S, o->sx};
-            f512::row_inv<R>(V2, 1, o->sy, o->sy, o->sx, 1, er, done, st);
+            row_resid<R, kDataNW>(V2, o->sy, o->sx, er, done, st);
             k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
             return;
         }
@@ -668,16 +715,15 @@ struct SolverLaunch {
         const gj_op *o = sv->op[0];
         const int *done = &sv->S->done;
         if constexpr (std::is_same_v<R, float>) if (fast) {
-            LoadPair<R> lv{F.v[0], F.v[1], o->sx};
-            f512::row_fwd<R>(V2, 1, o->sy, o->sy, o->sx, 1, lv, done, st);
-            f512::col_adj<R>(V2, o->col_grid, done, st);
+            using namespace f512;
+            col_adj<R>(V2, o->col_grid, done, st);
             EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
-            f512::row_inv<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
+            row_inv<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
             ProDirection<R> pd{F, sv->S, o->nx, o->ny};
-            f512::row_fwd<R>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
+            row_fwd<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
-            f512::row_inv<R>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
+            row_inv<R, kDataNW, kDataFPW>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
             k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
             head(st);
             return;
@@ -773,7 +819,7 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
     const size_t n = (size_t)o->nx * o->ny * o->nz, s = (size_t)o->sx * o->sy;
     cudaError_t e;
     if ((e = cudaMalloc(&sv->S, sizeof(SolverDev))) != cudaSuccess) { delete sv; return cuda_fail(e, "solver state"); }
-    if ((e = cudaMalloc(&sv->buf, (4 * n + 4 * s) * es)) != cudaSuccess) {
+    if ((e = cudaMalloc(&sv->buf, (4 * n + 4 * s + 2 * (size_t)o->nz) * es)) != cudaSuccess) {
         cudaFree(sv->S); delete sv; return cuda_fail(e, "solver vectors");
     }
     SolverDev h{};
@@ -798,6 +844,14 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
             k_reciprocal<double><<<64, 256, 0, st>>>((int)s, (const double *)sigma[i], (double *)wd);
         else
             k_reciprocal<float><<<64, 256, 0, st>>>((int)s, (const float *)sigma[i], (float *)wd);
+    }
+    // 1 / W_depth
+    for (int i = 0; i < 2; ++i) {
+        void *iw = static_cast<char *>(sv->buf) + (4 * n + 4 * s + (size_t)i * o->nz) * es;
+        if (o->prec == GJ_FP64)
+            k_reciprocal<double><<<1, 256, 0, st>>>(o->nz, (const double *)w_depth[i], (double *)iw);
+        else
+            k_reciprocal<float><<<1, 256, 0, st>>>(o->nz, (const float *)w_depth[i], (float *)iw);
     }
     if (o->prec == GJ_FP64) run_head<double>(sv, st); else run_head<float>(sv, st);
     e = cudaGetLastError();

@@ -232,8 +232,8 @@ static gj_status upload_twiddles(int N, gj_precision prec, void **out) {
 static void free_op_memory(gj_op *op) {
     if (!op) return;
     cudaFree(op->twx); cudaFree(op->twy); cudaFree(op->spec);
-    cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W);
-    op->twx = op->twy = op->spec = op->Z = op->Y = op->W = nullptr;
+    cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W); cudaFree(op->V);
+    op->twx = op->twy = op->spec = op->Z = op->Y = op->W = op->V = nullptr;
 }
 
 template <typename Rout>
@@ -404,10 +404,13 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
         op->ws_bytes = zb + wb + yb;
         if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMalloc(&op->V, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->Y, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        op->ws_bytes += wb;
         // rows beyond the prisms / stations must read as zero; counters start at zero
         if ((e = cudaMemset(op->Z, 0, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMemset(op->W, 0, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
+        if ((e = cudaMemset(op->V, 0, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMemset(op->Y, 0, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         op->P = op->Y;
         op->cnt = reinterpret_cast<int *>(static_cast<char *>(op->Y) + pb);

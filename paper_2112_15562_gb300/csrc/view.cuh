@@ -17,6 +17,7 @@ inline OpView<R> view_of(const gj_op *op) {
     v.Z = static_cast<cpx<R> *>(op->Z);
     v.Y = static_cast<cpx<R> *>(op->Y);
     v.W = static_cast<cpx<R> *>(op->W);
+    v.V = static_cast<cpx<R> *>(op->V);
     return v;
 }
 
