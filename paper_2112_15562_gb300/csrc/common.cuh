@@ -15,6 +15,13 @@ template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a,
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// Blackwell paired FP32 arithmetic: one instruction per complex add or subtract
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // a - b, exact product by -1
+}
+#endif
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

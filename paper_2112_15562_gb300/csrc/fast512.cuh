@@ -111,20 +111,26 @@ __device__ __forceinline__ cpx<R> w32c(int j) {  // W32^j for 0 <= j < 16 (j kno
 template <typename R>
 struct LaneTw {
     cpx<R> lo[4], hi[4], pre;
-    __device__ void load(const cpx<R> *tw512) {  // tw512[k] = W512^k
+    __device__ void load(const cpx<R> *__restrict__ tw512) {  // tw512[k] = W512^k (global, read-only)
         const int l = threadIdx.x & 15;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            lo[k] = tw512[(2 * l * k) & 511];
-            hi[k] = tw512[(8 * l * k) & 511];
+            lo[k] = __ldg(tw512 + ((2 * l * k) & 511));
+            hi[k] = __ldg(tw512 + ((8 * l * k) & 511));
         }
-        pre = tw512[l];
+        pre = __ldg(tw512 + l);
     }
     template <bool INV> __device__ __forceinline__ cpx<R> mul256(cpx<R> a, int k) const {
         const cpx<R> w = cmul(lo[k & 3], hi[k >> 2]);
         return INV ? cmulc(a, w) : cmul(a, w);
     }
 };
+
+// Parity-split position of spectrum index k (0 <= k < 512) in a staging row, so
+// that the lanes of a half-warp (one parity, consecutive k/2) hit consecutive words.
+__device__ __forceinline__ int ppos(int k) { return ((k & 1) << 8) | (k >> 1); }
+// and of column kx (0 <= kx <= 256) in the inverse passes' staging tile
+__device__ __forceinline__ int kpos(int kx) { return (kx & 1) ? 129 + (kx >> 1) : (kx >> 1); }
 
 // swizzled 16 x 16 tile of one half-warp: entry (row, col) at row*16 + (col ^ row)
 __device__ __forceinline__ int swz(int row, int col) { return row * 16 + (col ^ row); }
@@ -286,8 +292,8 @@ __device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const Vie
     const C *row = tile + f * (N + 1);
     const int kstep = blockDim.x / FFTS;
     for (int kx = threadIdx.x / FFTS; kx < NC; kx += kstep) {
-        const C zk = row[kx];
-        const C zm = row[(N - kx) & (N - 1)];
+        const C zk = row[ppos(kx)];
+        const C zm = row[ppos((N - kx) & (N - 1))];
         if (ha) oa[kx * H] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
         if (hb) ob[kx * H] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     }
@@ -320,11 +326,10 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
     C *xb = tile + FFTS * (N + 1);              // per warp 512
     C *tws = xb + NW * N;                       // W512 table
     __shared__ double red[32];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
     pro.init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(tws);
+    tw.load(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
     C *buf = xb + warp * N;
@@ -335,7 +340,12 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
         pair_lines(joint, base, f, nlines, la, lb, ha, hb);
         R a[8], b[8];
         if (ha) {
-            pro.template fetch_batch<8>(la, lb, hb, lane, 32, n_in, a, b);
+            // two batches of four keep the prologue's registers below the spill point
+            R a0[4], b0[4], a1[4], b1[4];
+            pro.template fetch_batch<4>(la, lb, hb, lane, 32, n_in, a0, b0);
+            pro.template fetch_batch<4>(la, lb, hb, lane + 128, 32, n_in, a1, b1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
@@ -344,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
         fwd512_from_lines<R>(a, b, buf, tw, v);
         const int lam = 2 * l + h;
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + lam + 32 * k1] = v[k1];
+        for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + ppos(lam + 32 * k1)] = v[k1];
     }
     __syncthreads();
     write_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, out_sel);
@@ -376,7 +386,7 @@ __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int kx = kb + u * kstep;
-            if (kx < NC) tile[kx * P + s] = val[u];
+            if (kx < NC) tile[kpos(kx) * P + s] = val[u];
         }
     }
 }
@@ -396,7 +406,7 @@ __device__ __forceinline__ void inv512_to_lines(const cpx<R> *tile, int sa, int 
         const int k = lam + 32 * k1;
         const bool lo = k <= H;
         const int kk = lo ? k : N - k;
-        C A = tile[kk * P + sa], B = tile[kk * P + sb];
+        C A = tile[kpos(kk) * P + sa], B = tile[kpos(kk) * P + sb];
         if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
         v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
     }
@@ -427,13 +437,12 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
     C *xb = tile + NC * (2 * FFTS + 1);
     C *tws = xb + NW * N;
     __shared__ double red[32];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
     epi.init();
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
     stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(tws);
+    tw.load(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C *buf = xb + warp * N;
     for (int s2 = 0; s2 < FPW; ++s2) {
@@ -445,7 +454,13 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
         int la, lb;
         bool ha, hb;
         pair_lines(joint, base, f, nlines, la, lb, ha, hb);
-        if (ha) epi.template store_batch<8>(la, lb, hb, lane, 32, n_out, a, b);
+        if (ha) {
+            R a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
+            epi.template store_batch<4>(la, lb, hb, lane, 32, n_out, a0, b0);
+            epi.template store_batch<4>(la, lb, hb, lane + 128, 32, n_out, a1, b1);
+        }
     }
     epi.flush(red);
 }
@@ -465,13 +480,12 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
     C *xb = tile + (NC * (2 * FFTS + 1) > FFTS * (N + 1) ? NC * (2 * FFTS + 1) : FFTS * (N + 1));
     C *tws = xb + NW * N;
     __shared__ double red[32];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twx[i];
     epi.init();
     const int base = blockIdx.x * FFTS;
     stage_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 1);
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(tws);
+    tw.load(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     C *buf = xb + warp * N;
     const int f = warp;
@@ -490,7 +504,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
     __syncthreads();  // every warp is done reading the staged input
     const int lam = 2 * l + h;
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + lam + 32 * k1] = v[k1];
+    for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + ppos(lam + 32 * k1)] = v[k1];
     __syncthreads();
     write_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 2);
     epi.flush(red);
@@ -514,13 +528,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
     C *xbuf = reinterpret_cast<C *>(wbase + STAGES * (ZB + TB));   // 512
     C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * (ZB + TB) + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twy[i];
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(tws);
+    tw.load(V.op[0].twy);
     const int nz = V.op[0].nz, sy = V.op[0].sy;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
@@ -629,13 +642,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
     C *xbuf = reinterpret_cast<C *>(wbase + STAGES * TB);
     C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * TB + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = V.op[0].twy[i];
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(tws);
+    tw.load(V.op[0].twy);
     const int nz = V.op[0].nz, ny = V.op[0].ny;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
