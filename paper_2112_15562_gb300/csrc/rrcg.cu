@@ -577,9 +577,14 @@ struct gj_rrcg {
     cudaStream_t graph_stream = nullptr;
     int profile = 0;
     std::vector<ProfilePair> eager_pairs;   // recorded since the last read
-    std::vector<ProfilePair> graph_pairs;   // owned by the captured graph
+    std::vector<ProfilePair> graph_pairs;   // unused: events inside a graph cannot be timed
     std::vector<ProfilePair> free_pairs;
     bool capturing = false;
+    // profiled graph form: the body captured as segments cut around each timed launch
+    std::vector<cudaGraph_t> seg_graph;
+    std::vector<cudaGraphExec_t> seg_exec;
+    cudaStream_t cap_stream = nullptr;   // stream being captured while segmenting
+    cudaError_t cap_err = cudaSuccess;
 };
 
 namespace gj {
@@ -589,6 +594,16 @@ static ProfilePair take_pair(gj_rrcg *sv) {
     if (!sv->free_pairs.empty()) { p = sv->free_pairs.back(); sv->free_pairs.pop_back(); }
     else { cudaEventCreate(&p.a); cudaEventCreate(&p.b); }
     return p;
+}
+
+// Ends the capture in progress, keeps the captured segment, and begins the next.
+static void cut_segment(gj_rrcg *sv, cudaStream_t st) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) sv->seg_graph.push_back(g);
+    else if (sv->cap_err == cudaSuccess) sv->cap_err = e;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess && sv->cap_err == cudaSuccess) sv->cap_err = e;
 }
 
 template <typename R>
@@ -659,14 +674,18 @@ struct SolverLaunch {
         const gj_op *o = sv->op[0];
         if constexpr (std::is_same_v<R, float>) if (fast) {
             ProfilePair pp{};
-            if (sv->profile) {
+            if (sv->profile && sv->capturing) {
+                cut_segment(sv, st);  // the timed launch gets a segment of its own
+            } else if (sv->profile) {
                 pp = take_pair(sv);
                 cudaEventRecord(pp.a, st);
             }
             f512::col_fwd<R>(V2, o->col_grid, &sv->S->done, st);
-            if (sv->profile) {
+            if (sv->profile && sv->capturing) {
+                cut_segment(sv, st);
+            } else if (sv->profile) {
                 cudaEventRecord(pp.b, st);
-                (sv->capturing ? sv->graph_pairs : sv->eager_pairs).push_back(pp);
+                sv->eager_pairs.push_back(pp);
             }
             return;
         }
@@ -675,14 +694,14 @@ struct SolverLaunch {
         cudaMemsetAsync(v1.Y, 0, (size_t)o->Ny * o->ncol * cs, st);
         const int nt = (o->ncol + C - 1) / C;
         ProfilePair pp{};
-        if (sv->profile) {
+        if (sv->profile && !sv->capturing) {
             pp = take_pair(sv);
             cudaEventRecord(pp.a, st);
         }
         k_col_fwd_mac<R><<<dim3(nt, (o->nz + L - 1) / L, 2), 256, msm, st>>>(v0, v1, C, L, &sv->S->done);
-        if (sv->profile) {
+        if (sv->profile && !sv->capturing) {
             cudaEventRecord(pp.b, st);
-            (sv->capturing ? sv->graph_pairs : sv->eager_pairs).push_back(pp);
+            sv->eager_pairs.push_back(pp);
         }
         k_col_inv<R><<<dim3(nt, 2), 256, csm, st>>>(v0, v1, C, &sv->S->done);
     }
@@ -867,15 +886,51 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
 extern "C" gj_status gj_rrcg_iterate(gj_rrcg *sv, int iters, int use_graph, gj_stream_t stream) {
     if (!sv || iters < 0) { set_error("gj_rrcg_iterate: bad argument"); return GJ_ERR_ARG; }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (use_graph && sv->profile && sv->prec == GJ_FP32_MIXED && sv->op[0]->fast) {
+        // segments [.. | col | .. | col | ..] with stream events around the column launches
+        if (sv->seg_exec.empty()) {
+            cudaStream_t cap;
+            GJ_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            sv->capturing = true;
+            sv->cap_err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (sv->cap_err == cudaSuccess) {
+                run_body<float>(sv, cap);
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(cap, &g);
+                if (e == cudaSuccess) sv->seg_graph.push_back(g);
+                else if (sv->cap_err == cudaSuccess) sv->cap_err = e;
+            }
+            sv->capturing = false;
+            cudaStreamDestroy(cap);
+            if (sv->cap_err != cudaSuccess || sv->seg_graph.size() != 5) {
+                for (auto g : sv->seg_graph) cudaGraphDestroy(g);
+                sv->seg_graph.clear();
+                return cuda_fail(sv->cap_err != cudaSuccess ? sv->cap_err : cudaErrorUnknown, "rrcg segment capture");
+            }
+            for (auto g : sv->seg_graph) {
+                cudaGraphExec_t x;
+                GJ_CUDA(cudaGraphInstantiate(&x, g, 0));
+                sv->seg_exec.push_back(x);
+            }
+        }
+        for (int it = 0; it < iters; ++it) {
+            for (int sgi = 0; sgi < 5; ++sgi) {
+                ProfilePair pp{};
+                if (sgi == 1 || sgi == 3) {
+                    pp = take_pair(sv);
+                    GJ_CUDA(cudaEventRecord(pp.a, st));
+                }
+                GJ_CUDA(cudaGraphLaunch(sv->seg_exec[sgi], st));
+                if (sgi == 1 || sgi == 3) {
+                    GJ_CUDA(cudaEventRecord(pp.b, st));
+                    sv->eager_pairs.push_back(pp);
+                }
+            }
+        }
+        return GJ_OK;
+    }
     if (use_graph) {
         if (!sv->exec) {
-            if (sv->profile)
-                for (int i = 0; i < 4; ++i) {
-                    ProfilePair p;
-                    GJ_CUDA(cudaEventCreate(&p.a));
-                    GJ_CUDA(cudaEventCreate(&p.b));
-                    sv->free_pairs.push_back(p);
-                }
             cudaStream_t cap;
             GJ_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             sv->capturing = true;
@@ -934,11 +989,6 @@ extern "C" int gj_rrcg_done(gj_rrcg *sv, gj_stream_t stream) {
 
 extern "C" gj_status gj_rrcg_profile(gj_rrcg *sv, int enable) {
     if (!sv) { set_error("gj_rrcg_profile: NULL solver"); return GJ_ERR_ARG; }
-    if (enable && sv->exec && sv->graph_pairs.empty()) {
-        // the graph was captured without events: capture again
-        cudaGraphExecDestroy(sv->exec); sv->exec = nullptr;
-        cudaGraphDestroy(sv->graph); sv->graph = nullptr;
-    }
     sv->profile = enable ? 1 : 0;
     return GJ_OK;
 }
@@ -960,7 +1010,6 @@ extern "C" gj_status gj_rrcg_profile_read(gj_rrcg *sv, int *launches, double *to
     };
     gj_status rc = acc(sv->eager_pairs);
     if (rc != GJ_OK) return rc;
-    if (sv->exec) { rc = acc(sv->graph_pairs); if (rc != GJ_OK) return rc; }
     for (auto &p : sv->eager_pairs) sv->free_pairs.push_back(p);
     sv->eager_pairs.clear();
     *launches = cnt;
@@ -973,6 +1022,8 @@ extern "C" void gj_rrcg_destroy(gj_rrcg *sv) {
     cudaDeviceSynchronize();
     if (sv->exec) cudaGraphExecDestroy(sv->exec);
     if (sv->graph) cudaGraphDestroy(sv->graph);
+    for (auto x : sv->seg_exec) cudaGraphExecDestroy(x);
+    for (auto g : sv->seg_graph) cudaGraphDestroy(g);
     for (auto *v : {&sv->eager_pairs, &sv->graph_pairs, &sv->free_pairs})
         for (auto &p : *v) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     cudaFree(sv->S);
