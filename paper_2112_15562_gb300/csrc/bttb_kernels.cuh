@@ -27,6 +27,7 @@ struct OpView {
     cpx<R> *Y;           // [Ny][ncol]     summed spectrum / residual spectrum
     cpx<R> *W;           // [max(sy, ...)][ncol]  inverse-column output / residual rows
     cpx<R> *V;           // fast path: residual-row spectra [ncol][256] (unused otherwise)
+    int real_spec;       // fast path: spec holds only real parts, R[nz][ncol][Ny] (even table)
 };
 
 // How real lines are paired into complex transforms.

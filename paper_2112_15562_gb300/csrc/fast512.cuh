@@ -548,9 +548,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
         const long long col = t / nz;
         const int fld = (int)(col / NC), kx = (int)(col % NC);
         const OpView<R> &op = V.op[fld];
-        mbar_expect(&bars[warp][s], ZB + TB);
-        bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
-        bulk_load(ts + s * N, op.spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+        if (op.real_spec) {
+            mbar_expect(&bars[warp][s], ZB + TB / 2);
+            bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + ((size_t)r * NC + kx) * N, TB / 2,
+                      &bars[warp][s]);
+        } else {
+            mbar_expect(&bars[warp][s], ZB + TB);
+            bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
+            bulk_load(ts + s * N, op.spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+        }
     };
     if (lane == 0)
         for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
@@ -566,15 +573,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
         C v[16], tv[16];
+        const bool real_t = V.op[(int)((t / nz) / NC)].real_spec;
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = zs[s * H + l + 16 * j];
+        if (real_t) {
+            const R *tr = reinterpret_cast<const R *>(ts + s * N);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) tv[k1] = ts[s * N + lam + 32 * k1];
+            for (int k1 = 0; k1 < 16; ++k1) tv[k1] = mk<C>(tr[lam + 32 * k1], R(0));
+        } else {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) tv[k1] = ts[s * N + lam + 32 * k1];
+        }
         __syncwarp();
         if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
         fwd512<R>(v, xbuf, tw);
+        if (real_t) {
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], tv[k1]));
+            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = mk<C>(acc[k1].x + v[k1].x * tv[k1].x, acc[k1].y + v[k1].y * tv[k1].x);
+        } else {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], tv[k1]));
+        }
         const int r = (int)(t % nz);
         if (r == nz - 1 || t == t1 - 1) {
             // end of this warp's part of column `col`
@@ -661,8 +680,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
         const int r = (int)(t % nz);
         const long long col = t / nz;
         const int fld = (int)(col / NC), kx = (int)(col % NC);
-        mbar_expect(&bars[warp][s], TB);
-        bulk_load(ts + s * N, V.op[fld].spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+        if (V.op[fld].real_spec) {
+            mbar_expect(&bars[warp][s], TB / 2);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[fld].spec) + ((size_t)r * NC + kx) * N, TB / 2,
+                      &bars[warp][s]);
+        } else {
+            mbar_expect(&bars[warp][s], TB);
+            bulk_load(ts + s * N, V.op[fld].spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+        }
     };
     if (lane == 0)
         for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
@@ -688,8 +713,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
         C v[16];
+        if (op.real_spec) {
+            const R *tr = reinterpret_cast<const R *>(ts + s * N);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], ts[s * N + lam + 32 * k1]);
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const R tt = tr[lam + 32 * k1];
+                v[k1] = mk<C>(vh[k1].x * tt, vh[k1].y * tt);
+            }
+        } else {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], ts[s * N + lam + 32 * k1]);
+        }
         __syncwarp();
         if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
         C out[8];

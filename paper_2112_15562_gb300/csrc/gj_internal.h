@@ -29,6 +29,7 @@ struct gj_op {
     // 512 x 512 fast path (FP32, <= 256 prisms and stations per direction):
     // transposed spectra and intermediates, layer-sum partials and counters
     bool fast = false;
+    bool real_spec = false;  // fast path: the table is even in both offsets, its spectrum is real
     void *P = nullptr;     // [ncol][slots][512] complex
     int *cnt = nullptr;    // [ncol] arrival counters
     int *err = nullptr;    // device error word (bounded waits)

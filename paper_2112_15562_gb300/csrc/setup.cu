@@ -102,7 +102,7 @@ struct LoadTable {
 // Column pass of the setup: spec[r] = FFT_y of the row-pass output of layer r.
 template <typename Rout>
 __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const double2 *Zs, cpx<Rout> *spec, int C,
-                                                  int transposed) {
+                                                  int transposed, int real_only) {
     using Cx = double2;
     const int c0 = blockIdx.x * C;
     const int r = blockIdx.y;
@@ -124,7 +124,10 @@ __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const doubl
         const int c = it % C, ky = it / C;
         if (c0 + c < ncol) {
             const size_t at = transposed ? (size_t)(c0 + c) * Ny + ky : (size_t)ky * ncol + c0 + c;
-            Sr[at] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
+            if (real_only)  // the imaginary part is zero in exact arithmetic; keep the real part
+                reinterpret_cast<Rout *>(spec)[(size_t)r * Ny * ncol + at] = (Rout)X[it].x;
+            else
+                Sr[at] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
         }
     }
 }
@@ -312,7 +315,8 @@ static gj_status build_spectra(gj_op *op, cudaStream_t st) {
     const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
     cudaFuncSetAttribute(k_col_spec<Rout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
     dim3 g((op->ncol + C - 1) / C, op->nz);
-    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C, op->fast ? 1 : 0);
+    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C, op->fast ? 1 : 0,
+                                         op->real_spec ? 1 : 0);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(zw_d);
@@ -377,13 +381,16 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         op->col_grid = std::max(1, sms);
         op->slots = std::max(fast_slots(1, G.nz, op->col_grid), fast_slots(2, G.nz, op->col_grid));
+        // gravity over a station grid that covers the prisms with no offset: the table
+        // is even in both offsets, so its spectrum is real
+        op->real_spec = field == GJ_GRAVITY && G.sx == G.nx && G.sy == G.ny && G.off_x == 0 && G.off_y == 0;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     gj_status rc;
     cudaError_t e;
     if ((rc = upload_twiddles(Nx, prec, &op->twx)) != GJ_OK) goto fail;
     if ((rc = upload_twiddles(Ny, prec, &op->twy)) != GJ_OK) goto fail;
-    op->spec_bytes = (size_t)G.nz * Ny * op->ncol * cs;
+    op->spec_bytes = (size_t)G.nz * Ny * op->ncol * (op->real_spec ? cs / 2 : cs);
     if ((e = cudaMalloc(&op->spec, op->spec_bytes)) != cudaSuccess) { rc = cuda_fail(e, "spectra"); goto fail; }
     rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
     if (rc != GJ_OK) goto fail;

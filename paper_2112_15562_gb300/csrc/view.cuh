@@ -18,6 +18,7 @@ inline OpView<R> view_of(const gj_op *op) {
     v.Y = static_cast<cpx<R> *>(op->Y);
     v.W = static_cast<cpx<R> *>(op->W);
     v.V = static_cast<cpx<R> *>(op->V);
+    v.real_spec = op->real_spec ? 1 : 0;
     return v;
 }
 
