@@ -242,6 +242,20 @@ gj_status gj_rrcg_profile(gj_rrcg *solver, int enable);
 gj_status gj_rrcg_profile_read(gj_rrcg *solver, int *launches, double *total_ms);
 void gj_rrcg_destroy(gj_rrcg *solver);
 
+/*
+ * Batched form: several independent joint inversions, of any sizes and
+ * precisions, advanced together.  gj_rrcg_batch_create captures one CUDA graph
+ * whose parallel branches are one iteration of each solver (as in
+ * gj_rrcg_iterate); gj_rrcg_batch_step replays it `iters` times on `stream`, so
+ * one launch advances every problem by one RRCG iteration (solvers that have
+ * stopped do no work).  The solvers stay owned by the caller and must outlive
+ * the batch; while a batch exists, do not step its solvers on other streams.
+ */
+typedef struct gj_rrcg_batch gj_rrcg_batch;
+gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj_stream_t stream, gj_rrcg_batch **out);
+gj_status gj_rrcg_batch_step(gj_rrcg_batch *batch, int iters, gj_stream_t stream);
+void gj_rrcg_batch_destroy(gj_rrcg_batch *batch);
+
 /* Last error message of the calling thread ("" if none). */
 const char *gj_last_error(void);
 

@@ -86,6 +86,9 @@ def load() -> ct.CDLL:
         "gj_rrcg_profile": (i32, [vp, i32]),
         "gj_rrcg_profile_read": (i32, [vp, ct.POINTER(i32), ct.POINTER(d)]),
         "gj_rrcg_destroy": (None, [vp]),
+        "gj_rrcg_batch_create": (i32, [pp, i32, vp, pp]),
+        "gj_rrcg_batch_step": (i32, [vp, i32, vp]),
+        "gj_rrcg_batch_destroy": (None, [vp]),
         "gj_last_error": (ct.c_char_p, []),
         "gj_version": (ct.c_char_p, []),
     }

@@ -269,3 +269,32 @@ def rrcg_joint_solve_host(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, 
     bin_ = sum(t.numel() * t.element_size() for t in pin)
     bout = sum(t.numel() * t.element_size() for t in out)
     return [o_.numpy() for o_ in out], rep, bin_, bout
+
+
+class Batch:
+    """Several Solvers advanced together by one CUDA graph (gj_rrcg_batch_*)."""
+
+    def __init__(self, solvers: Sequence[Solver], stream=None):
+        lib = load()
+        self.solvers = list(solvers)
+        arr = (ct.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        out = ct.c_void_p()
+        check(lib.gj_rrcg_batch_create(arr, len(self.solvers), _stream(stream), ct.byref(out)))
+        self._h = out
+
+    def step(self, iters: int = 1, stream=None):
+        check(load().gj_rrcg_batch_step(self._h, int(iters), _stream(stream)))
+
+    def all_done(self, stream=None) -> bool:
+        return all(s.done(stream) for s in self.solvers)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().gj_rrcg_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -85,4 +85,23 @@ __device__ __forceinline__ void block_accumulate(const A *acc, double *out, doub
     }
 }
 
+// Allows launches of `f` with any dynamic shared memory up to the device's opt-in
+// maximum less the kernel's static shared memory.  The attribute belongs to the
+// function, not to a launch, so setting it to the maximum keeps callers with
+// different sizes from overriding each other.
+template <typename F>
+inline cudaError_t allow_max_smem(F *f) {
+    static int optin = -1;
+    if (optin < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
+    }
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn > 0 ? dyn : 0);
+}
+
 }  // namespace gj

@@ -26,23 +26,20 @@ constexpr int kCellNW = 8, kCellFPW = 2, kDataNW = 4, kDataFPW = 1;
 
 template <typename R, class Pro, int NW, int FPW>
 inline void set_row_fwd_attr() {
-    cudaFuncSetAttribute(k_row_fwd512<R, Pro, NW, FPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_row_fwd<R, NW, FPW>());
+    allow_max_smem(k_row_fwd512<R, Pro, NW, FPW>);
 }
 template <typename R, class Epi, int NW, int FPW>
 inline void set_row_inv_attr() {
-    cudaFuncSetAttribute(k_row_inv512<R, Epi, NW, FPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_row_inv<R, NW, FPW>());
+    allow_max_smem(k_row_inv512<R, Epi, NW, FPW>);
 }
 template <typename R, class Epi, int NW>
 inline void set_row_resid_attr() {
-    cudaFuncSetAttribute(k_row_resid512<R, Epi, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_row_resid<R, NW>());
+    allow_max_smem(k_row_resid512<R, Epi, NW>);
 }
 template <typename R>
 inline void set_col_attr() {
-    cudaFuncSetAttribute(k_col_fwd512<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col_fwd<R>());
-    cudaFuncSetAttribute(k_col_adj512<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col_adj<R>());
+    allow_max_smem(k_col_fwd512<R>);
+    allow_max_smem(k_col_adj512<R>);
 }
 
 // out_sel / in_sel: 0 = Z, 1 = W, 2 = V

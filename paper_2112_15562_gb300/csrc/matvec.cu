@@ -13,7 +13,7 @@ static void launch_forward(const gj_op *o, const R *m, R *d, cudaStream_t st) {
     PairMap pm{o->nz * o->ny, 0};
     const int P = o->P_row;
     const size_t rsm = row_smem(o->Nx, P, cs);
-    cudaFuncSetAttribute(k_row_fwd<R, LoadPlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
     const int npr = (pm.nlines + 1) / 2;
     k_row_fwd<R, LoadPlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
                                                                     LoadPlain<R>{m, m, o->nx}, nullptr);
@@ -22,16 +22,16 @@ static void launch_forward(const gj_op *o, const R *m, R *d, cudaStream_t st) {
     const int C = o->C_col;
     const int nt = (o->ncol + C - 1) / C;
     const size_t msm = col_smem(o->Ny, C, 3, cs);
-    cudaFuncSetAttribute(k_col_fwd_mac<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+    allow_max_smem(k_col_fwd_mac<R>);
     k_col_fwd_mac<R><<<dim3(nt, (o->nz + o->L_grp - 1) / o->L_grp, 1), 256, msm, st>>>(v, v, C, o->L_grp, nullptr);
     // inverse columns
     const size_t ism = col_smem(o->Ny, C, 2, cs);
-    cudaFuncSetAttribute(k_col_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    allow_max_smem(k_col_inv<R>);
     k_col_inv<R><<<dim3(nt, 1), 256, ism, st>>>(v, v, C, nullptr);
     // inverse rows, cropped to the stations
     PairMap ps{o->sy, 0};
     const int nps = (ps.nlines + 1) / 2;
-    cudaFuncSetAttribute(k_row_inv<R, StorePlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_max_smem(k_row_inv<R, StorePlain<R>>);
     k_row_inv<R, StorePlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
                                                                      StorePlain<R>{d, d, o->sx}, nullptr);
 }
@@ -45,19 +45,19 @@ static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
     // rows of the residual -> W
     PairMap ps{o->sy, 0};
     const int nps = (ps.nlines + 1) / 2;
-    cudaFuncSetAttribute(k_row_fwd<R, LoadPlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
     k_row_fwd<R, LoadPlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
                                                                     LoadPlain<R>{r, r, o->sx}, nullptr);
     const int C = o->C_col;
     const int nt = (o->ncol + C - 1) / C;
     const size_t sm2 = col_smem(o->Ny, C, 2, cs);
-    cudaFuncSetAttribute(k_col_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    allow_max_smem(k_col_fft<R>);
     k_col_fft<R><<<dim3(nt, 1), 256, sm2, st>>>(v, v, C, nullptr);
-    cudaFuncSetAttribute(k_col_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    allow_max_smem(k_col_adj<R>);
     k_col_adj<R><<<dim3(nt, o->nz, 1), 256, sm2, st>>>(v, v, C, nullptr);
     PairMap pm{o->nz * o->ny, 0};
     const int npr = (pm.nlines + 1) / 2;
-    cudaFuncSetAttribute(k_row_inv<R, StorePlain<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_max_smem(k_row_inv<R, StorePlain<R>>);
     k_row_inv<R, StorePlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
                                                                      StorePlain<R>{g, g, o->nx}, nullptr);
 }

@@ -647,6 +647,11 @@ struct SolverLaunch {
     }
 
     void set_attributes() {
+        // Load every kernel of an iteration now: with lazy module loading, the first
+        // launch of a kernel inside a stream capture would invalidate the capture.
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_scalars_after_direction);
+        cudaFuncGetAttributes(&fa, k_scalars_after_residual);
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
             set_row_fwd_attr<R, ProModel<R>, kCellNW, kCellFPW>();
@@ -657,16 +662,16 @@ struct SolverLaunch {
             set_col_attr<R>();
             return;
         }
-        cudaFuncSetAttribute(k_row_fwd<R, ProModel<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_row_fwd<R, ProDirection<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_row_fwd<R, LoadPair<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_row_inv<R, EpiResidual<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_row_inv<R, EpiGradient<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_row_inv<R, EpiQNorm<R>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        cudaFuncSetAttribute(k_col_fwd_mac<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
-        cudaFuncSetAttribute(k_col_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-        cudaFuncSetAttribute(k_col_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-        cudaFuncSetAttribute(k_col_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        allow_max_smem(k_row_fwd<R, ProModel<R>>);
+        allow_max_smem(k_row_fwd<R, ProDirection<R>>);
+        allow_max_smem(k_row_fwd<R, LoadPair<R>>);
+        allow_max_smem(k_row_inv<R, EpiResidual<R>>);
+        allow_max_smem(k_row_inv<R, EpiGradient<R>>);
+        allow_max_smem(k_row_inv<R, EpiQNorm<R>>);
+        allow_max_smem(k_col_fwd_mac<R>);
+        allow_max_smem(k_col_inv<R>);
+        allow_max_smem(k_col_fft<R>);
+        allow_max_smem(k_col_adj<R>);
     }
 
     // Forward columns (Y = sum_r T^_r FFT_y(Z_r)) and inverse columns, both fields.
@@ -1058,4 +1063,82 @@ extern "C" gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrc
         return (gj_status)rep->status;
     }
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: several independent joint inversions (any sizes and precisions)
+// advanced by one CUDA graph whose branches are the solvers' iterations.
+
+struct gj_rrcg_batch {
+    std::vector<gj_rrcg *> sv;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj_stream_t stream,
+                                          gj_rrcg_batch **out) {
+    (void)stream;
+    if (!out || !solvers || count < 1) { set_error("gj_rrcg_batch_create: bad argument"); return GJ_ERR_ARG; }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i)
+        if (!solvers[i]) { set_error("gj_rrcg_batch_create: NULL solver"); return GJ_ERR_ARG; }
+    gj_rrcg_batch *b = new (std::nothrow) gj_rrcg_batch();
+    if (!b) { set_error("gj_rrcg_batch_create: host allocation failed"); return GJ_ERR_OOM; }
+    b->sv.assign(solvers, solvers + count);
+    // streams and events exist before the capture begins
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br(count, nullptr);
+    std::vector<cudaEvent_t> join(count, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ce = cudaEventRecord(fork, cap);
+        for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+            ce = cudaStreamWaitEvent(br[i], fork, 0);
+            if (ce != cudaSuccess) break;
+            gj_rrcg *sv = b->sv[i];
+            sv->capturing = true;
+            if (sv->prec == GJ_FP64) run_body<double>(sv, br[i]); else run_body<float>(sv, br[i]);
+            sv->capturing = false;
+            ce = cudaEventRecord(join[i], br[i]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, join[i], 0);
+        }
+        cudaError_t ee = cudaStreamEndCapture(cap, &b->graph);
+        e = ce != cudaSuccess ? ce : ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    for (int i = 0; i < count; ++i) {
+        if (br[i]) cudaStreamDestroy(br[i]);
+        if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return cuda_fail(e, "gj_rrcg_batch_create");
+    }
+    *out = b;
+    return GJ_OK;
+}
+
+extern "C" gj_status gj_rrcg_batch_step(gj_rrcg_batch *b, int iters, gj_stream_t stream) {
+    if (!b || iters < 0) { set_error("gj_rrcg_batch_step: bad argument"); return GJ_ERR_ARG; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int it = 0; it < iters; ++it) GJ_CUDA(cudaGraphLaunch(b->exec, st));
+    return GJ_OK;
+}
+
+extern "C" void gj_rrcg_batch_destroy(gj_rrcg_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
 }

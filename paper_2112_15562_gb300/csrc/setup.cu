@@ -309,11 +309,11 @@ static gj_status build_spectra(gj_op *op, cudaStream_t st) {
     const int P = pick_row_pairs(op->Nx, sizeof(double2));
     const int npairs = (pm.nlines + 1) / 2;
     const size_t rsm = row_smem(op->Nx, P, sizeof(double2));
-    cudaFuncSetAttribute(k_row_fwd<double, LoadTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    allow_max_smem(k_row_fwd<double, LoadTable>);
     k_row_fwd<double, LoadTable><<<(npairs + P - 1) / P, 256, rsm, st>>>(v, pm, op->Nx, P, Zs, Zs, lt, nullptr);
     const int C = pick_col_tile(op->Ny, sizeof(double2), 2);
     const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
-    cudaFuncSetAttribute(k_col_spec<Rout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    allow_max_smem(k_col_spec<Rout>);
     dim3 g((op->ncol + C - 1) / C, op->nz);
     k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C, op->fast ? 1 : 0,
                                          op->real_spec ? 1 : 0);
