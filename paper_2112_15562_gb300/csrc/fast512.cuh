@@ -23,8 +23,8 @@ namespace gj {
 namespace f512 {
 
 constexpr int N = 512, H = 256, NC = 257;
-constexpr int WARPS = 8;          // warps per CTA in every fast kernel
-constexpr int STAGES = 3;         // TMA ring depth of the column kernels
+constexpr int CWARPS = 12;        // warps per CTA of the persistent column kernels (one CTA per SM)
+constexpr int CSTAGES = 2;        // TMA ring depth per warp of the column kernels
 constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
 
 // ---------------------------------------------------------------------------
@@ -229,12 +229,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 }
 
 // After a timed-out wait at item t_fail, wait (bounded) for the copies this warp
-// issued and has not consumed (items t_fail .. t_fail + STAGES - 1) so that no bulk
-// copy lands in shared memory after the CTA exits.
+// issued and has not consumed (items t_fail .. t_fail + CSTAGES - 1) so that no
+// bulk copy lands in shared memory after the CTA exits.
 __device__ __forceinline__ void drain(uint64_t *bars, long long t_fail, long long t0, long long t1, int *err) {
-    for (long long t = t_fail; t < t1 && t < t_fail + STAGES; ++t) {
-        const int s = (int)((t - t0) % STAGES);
-        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+    for (long long t = t_fail; t < t1 && t < t_fail + CSTAGES; ++t) {
+        const int s = (int)((t - t0) % CSTAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         mbar_wait(bars + s, par, err);
     }
 }
@@ -516,20 +516,19 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
 // contiguous segments of the (field, kx, r) sequence; a column split across warps
 // is summed in segment order by the last warp to finish it.
 template <typename R>
-__global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int *done) {
+__global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const int *done) {
     using C = cpx<R>;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int ZB = H * sizeof(C), TB = N * sizeof(C);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
-    unsigned char *wbase = smem_raw + (size_t)warp * (STAGES * (ZB + TB) + N * sizeof(C));
-    C *zs = reinterpret_cast<C *>(wbase);                          // STAGES x 256
-    C *ts = reinterpret_cast<C *>(wbase + STAGES * ZB);            // STAGES x 512
-    C *xbuf = reinterpret_cast<C *>(wbase + STAGES * (ZB + TB));   // 512
-    C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * (ZB + TB) + N * sizeof(C)));
-    __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
+    unsigned char *wbase = smem_raw + (size_t)warp * (CSTAGES * (ZB + TB) + N * sizeof(C));
+    C *zs = reinterpret_cast<C *>(wbase);                          // CSTAGES x 256
+    C *ts = reinterpret_cast<C *>(wbase + CSTAGES * ZB);            // CSTAGES x 512
+    C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * (ZB + TB));   // 512
+    __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
     if (lane == 0)
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
+        for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
@@ -537,13 +536,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
     const int nz = V.op[0].nz, sy = V.op[0].sy;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
-    const long long Wt = seg_warps((long long)gridDim.x * WARPS, T);
-    const long long w = (long long)blockIdx.x * WARPS + warp;
+    const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
+    const long long w = (long long)blockIdx.x * CWARPS + warp;
     if (w >= Wt) return;
     const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
     auto issue = [&](long long t) {
-        const int s = (int)((t - t0) % STAGES);
+        const int s = (int)((t - t0) % CSTAGES);
         const int r = (int)(t % nz);
         const long long col = t / nz;
         const int fld = (int)(col / NC), kx = (int)(col % NC);
@@ -560,7 +559,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
         }
     };
     if (lane == 0)
-        for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
+        for (long long t = t0; t < t1 && t < t0 + CSTAGES; ++t) issue(t);
     C acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = czero<C>();
@@ -568,32 +567,29 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
     long long t_fail = t1;
     long long seg_start = t0;
     for (long long t = t0; t < t1 && ok; ++t) {
-        const int s = (int)((t - t0) % STAGES);
-        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+        const int s = (int)((t - t0) % CSTAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
-        C v[16], tv[16];
+        C v[16];
         const bool real_t = V.op[(int)((t / nz) / NC)].real_spec;
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = zs[s * H + l + 16 * j];
+        fwd512<R>(v, xbuf, tw);
+        // multiply by the layer's spectrum straight from the stage, then release it
         if (real_t) {
             const R *tr = reinterpret_cast<const R *>(ts + s * N);
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) tv[k1] = mk<C>(tr[lam + 32 * k1], R(0));
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const R tt = tr[lam + 32 * k1];
+                acc[k1] = mk<C>(acc[k1].x + v[k1].x * tt, acc[k1].y + v[k1].y * tt);
+            }
         } else {
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) tv[k1] = ts[s * N + lam + 32 * k1];
+            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], ts[s * N + lam + 32 * k1]));
         }
         __syncwarp();
-        if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
-        fwd512<R>(v, xbuf, tw);
-        if (real_t) {
-#pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = mk<C>(acc[k1].x + v[k1].x * tv[k1].x, acc[k1].y + v[k1].y * tv[k1].x);
-        } else {
-#pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], tv[k1]));
-        }
+        if (lane == 0 && t + CSTAGES < t1) issue(t + CSTAGES);
         const int r = (int)(t % nz);
         if (r == nz - 1 || t == t1 - 1) {
             // end of this warp's part of column `col`
@@ -650,19 +646,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_fwd512(View2<R> V, const int
 // Adjoint column pass: for each (field, kx, r),
 // Zt_r[kx][iy] = IFFT512(conj(St_r[kx]) . FFT512(Wt[kx]))[iy], iy < ny.
 template <typename R>
-__global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int *done) {
+__global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const int *done) {
     using C = cpx<R>;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TB = N * sizeof(C);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
-    unsigned char *wbase = smem_raw + (size_t)warp * (STAGES * TB + N * sizeof(C));
+    unsigned char *wbase = smem_raw + (size_t)warp * (CSTAGES * TB + N * sizeof(C));
     C *ts = reinterpret_cast<C *>(wbase);
-    C *xbuf = reinterpret_cast<C *>(wbase + STAGES * TB);
-    C *tws = reinterpret_cast<C *>(smem_raw + (size_t)WARPS * (STAGES * TB + N * sizeof(C)));
-    __shared__ __align__(8) uint64_t bars[WARPS][STAGES];
+    C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * TB);
+    __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
     if (lane == 0)
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[warp][s]);
+        for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
@@ -670,13 +665,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
     const int nz = V.op[0].nz, ny = V.op[0].ny;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
-    const long long Wt = seg_warps((long long)gridDim.x * WARPS, T);
-    const long long w = (long long)blockIdx.x * WARPS + warp;
+    const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
+    const long long w = (long long)blockIdx.x * CWARPS + warp;
     if (w >= Wt) return;
     const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
     auto issue = [&](long long t) {
-        const int s = (int)((t - t0) % STAGES);
+        const int s = (int)((t - t0) % CSTAGES);
         const int r = (int)(t % nz);
         const long long col = t / nz;
         const int fld = (int)(col / NC), kx = (int)(col % NC);
@@ -690,7 +685,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
         }
     };
     if (lane == 0)
-        for (long long t = t0; t < t1 && t < t0 + STAGES; ++t) issue(t);
+        for (long long t = t0; t < t1 && t < t0 + CSTAGES; ++t) issue(t);
     C vh[16];
     long long cur_col = -1;
     bool ok = true;
@@ -708,8 +703,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
             fwd512<R>(vh, xbuf, tw);
             cur_col = col;
         }
-        const int s = (int)((t - t0) % STAGES);
-        const uint32_t par = (uint32_t)(((t - t0) / STAGES) & 1);
+        const int s = (int)((t - t0) % CSTAGES);
+        const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
         C v[16];
@@ -725,7 +720,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_col_adj512(View2<R> V, const int
             for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], ts[s * N + lam + 32 * k1]);
         }
         __syncwarp();
-        if (lane == 0 && t + STAGES < t1) issue(t + STAGES);
+        if (lane == 0 && t + CSTAGES < t1) issue(t + CSTAGES);
         C out[8];
         inv512<R>(v, xbuf, tw, out);
         C *Zc = op.Z + ((size_t)r * NC + kx) * H;
@@ -750,10 +745,10 @@ template <typename R, int NW> inline size_t smem_row_resid() {
     return (t + NW * N + N) * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_fwd() {
-    return (size_t)WARPS * (STAGES * (H + N) + N) * sizeof(cpx<R>) + N * sizeof(cpx<R>);
+    return (size_t)CWARPS * (CSTAGES * (H + N) + N) * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_adj() {
-    return (size_t)WARPS * (STAGES * N + N) * sizeof(cpx<R>) + N * sizeof(cpx<R>);
+    return (size_t)CWARPS * (CSTAGES * N + N) * sizeof(cpx<R>);
 }
 
 }  // namespace f512

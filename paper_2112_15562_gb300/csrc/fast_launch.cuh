@@ -67,12 +67,12 @@ inline void row_resid(const View2<R> &V, int nlines, int n_out, const Epi &epi, 
 
 template <typename R>
 inline void col_fwd(const View2<R> &V, int grid, const int *done, cudaStream_t st) {
-    k_col_fwd512<R><<<grid, WARPS * 32, smem_col_fwd<R>(), st>>>(V, done);
+    k_col_fwd512<R><<<grid, CWARPS * 32, smem_col_fwd<R>(), st>>>(V, done);
 }
 
 template <typename R>
 inline void col_adj(const View2<R> &V, int grid, const int *done, cudaStream_t st) {
-    k_col_adj512<R><<<grid, WARPS * 32, smem_col_adj<R>(), st>>>(V, done);
+    k_col_adj512<R><<<grid, CWARPS * 32, smem_col_adj<R>(), st>>>(V, done);
 }
 
 }  // namespace f512

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 
+#include "fast512.cuh"
 #include "view.cuh"
 
 namespace gj {
@@ -195,7 +196,7 @@ bool fast_eligible(const gj_op *op) {
 // column kernels split the (field, kx, layer) sequence into balanced segments.
 int fast_slots(int nfield, int nz, int grid_ctas) {
     const long long T = (long long)nfield * 257 * nz;
-    const long long Wt = std::min((long long)grid_ctas * 8, T);
+    const long long Wt = std::min((long long)grid_ctas * f512::CWARPS, T);
     auto owner = [&](long long t) { return ((t + 1) * Wt + T - 1) / T - 1; };
     long long mx = 1;
     for (long long c = 0; c < (long long)nfield * 257; ++c)
