@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_row_fwd(OpView<R> op, PairMap pm, int n
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + N * P;
     C *tw = buf1 + N * P;
-    __shared__ double red[32];
+    __shared__ double red[128];
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = op.twx[i];
     pro.init();
     const int q0 = blockIdx.x * P;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_row_inv(OpView<R> op, PairMap pm, int n
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + N * P;
     C *tw = buf1 + N * P;
-    __shared__ double red[32];
+    __shared__ double red[128];
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = op.twx[i];
     epi.init();
     const int q0 = blockIdx.x * P;

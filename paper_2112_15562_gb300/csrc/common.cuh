@@ -58,7 +58,8 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 
 // Adds per-thread partials acc[0..K) into out[0..K) (one double atomic per
 // block per entry).  All K sums share one pass: warp shuffles, one barrier, and
-// the first warp finishes.  `scratch` holds at least 32 doubles (K * warps <= 32).
+// the first warp finishes.  `scratch` holds at least K * warps doubles (the fast
+// kernels reserve 128: K <= 4 with up to 32 warps).
 // All threads must call it.
 template <int K, typename A>
 __device__ __forceinline__ void block_accumulate(const A *acc, double *out, double *scratch) {

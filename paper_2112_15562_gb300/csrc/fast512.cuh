@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
     C *tile = reinterpret_cast<C *>(smem_raw);  // [FFTS][N + 1]
     C *xb = tile + FFTS * (N + 1);              // per warp 512
     C *tws = xb + NW * N;                       // W512 table
-    __shared__ double red[32];
+    __shared__ double red[128];
     pro.init();
     __syncthreads();
     LaneTw<R> tw;
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
     C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 FFTS + 1]
     C *xb = tile + NC * (2 * FFTS + 1);
     C *tws = xb + NW * N;
-    __shared__ double red[32];
+    __shared__ double red[128];
     epi.init();
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
     stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
     C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 NW + 1], later [NW][N + 1]
     C *xb = tile + (NC * (2 * FFTS + 1) > FFTS * (N + 1) ? NC * (2 * FFTS + 1) : FFTS * (N + 1));
     C *tws = xb + NW * N;
-    __shared__ double red[32];
+    __shared__ double red[128];
     epi.init();
     const int base = blockIdx.x * FFTS;
     stage_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 1);
