@@ -164,6 +164,13 @@ gj_status gj_gramian_value_grad_noalloc(int64_t n, gj_precision precision,
 
 /* Solver options (Eq. RRCG:1-8; Secs. 2.5, 2.6, 2.8). Index 0 = gravity, 1 = magnetic. */
 enum { GJ_SCALARS_AUTO = 0, GJ_SCALARS_JOINT = 1, GJ_SCALARS_PER_FIELD = 2 };
+/* Regulariser anchor of RRCG:4: the a-priori model W_k m_apr (default; the first
+ * variation, Eq. FirstVariation) or the previous weighted model W_{k-1} m_{k-1}
+ * (the difference as printed in RRCG:4). */
+enum { GJ_ANCHOR_APRIORI = 0, GJ_ANCHOR_PREVIOUS = 1 };
+/* Space of the Gramian coupling: the original models (RRCG:2-3, the paper's
+ * choice) or the weighted models W m (Eq. steepestascenta/b, Sec. 3.1.4). */
+enum { GJ_GRAMIAN_ORIGINAL = 0, GJ_GRAMIAN_WEIGHTED = 1 };
 
 typedef struct {
     int p[2];              /* Lp stabiliser, 1 (Eq. WL) or 2 (W_L = I, Sec. 3.1.5) */
@@ -176,6 +183,8 @@ typedef struct {
     int kmax;              /* maximum number of model updates */
     int stop_on_chi2;      /* 1: stop once both fields pass Eq. chi2 */
     int scalars;           /* GJ_SCALARS_*: AUTO = per field iff both lambdas are 0 */
+    int anchor;            /* GJ_ANCHOR_* */
+    int gramian_space;     /* GJ_GRAMIAN_*; with WEIGHTED the history's S_G is the weighted Gramian */
 } gj_rrcg_params;
 
 typedef struct {

@@ -41,7 +41,8 @@ class OpInfo(ct.Structure):
 class RRCGParams(ct.Structure):
     _fields_ = [("p", ct.c_int * 2), ("eps2", ct.c_double), ("alpha1", ct.c_double * 2), ("q", ct.c_double * 2),
                 ("alpha_min", ct.c_double * 2), ("lambda_", ct.c_double * 2), ("lo", ct.c_double * 2),
-                ("hi", ct.c_double * 2), ("kmax", ct.c_int), ("stop_on_chi2", ct.c_int), ("scalars", ct.c_int)]
+                ("hi", ct.c_double * 2), ("kmax", ct.c_int), ("stop_on_chi2", ct.c_int), ("scalars", ct.c_int),
+                ("anchor", ct.c_int), ("gramian_space", ct.c_int)]
 
 
 class RRCGReport(ct.Structure):

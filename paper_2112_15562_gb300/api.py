@@ -129,7 +129,7 @@ def gramian_value_grad(m1: torch.Tensor, m2: torch.Tensor, want_dirs: bool = Tru
 
 def solver_params(p=(1, 1), eps2=1e-9, alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(0.0, 0.0),
                   lam=(0.0, 0.0), lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=50, stop_on_chi2=True,
-                  scalars="auto") -> L.RRCGParams:
+                  scalars="auto", anchor="apriori", gramian_space="original") -> L.RRCGParams:
     P = L.RRCGParams()
     P.p[:] = [int(v) for v in p]
     P.eps2 = float(eps2)
@@ -142,6 +142,8 @@ def solver_params(p=(1, 1), eps2=1e-9, alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_
     P.kmax = int(kmax)
     P.stop_on_chi2 = 1 if stop_on_chi2 else 0
     P.scalars = {"auto": L.GJ_SCALARS_AUTO, "joint": L.GJ_SCALARS_JOINT, "per_field": L.GJ_SCALARS_PER_FIELD}[scalars]
+    P.anchor = {"apriori": 0, "previous": 1}[anchor]
+    P.gramian_space = {"original": 0, "weighted": 1}[gramian_space]
     return P
 
 

@@ -31,6 +31,8 @@ struct SolverDev {
     int k, done, status, pending_update;
     int sat[2];
     int kmax, stop_on_chi2, per_field;
+    int anchor;           // GJ_ANCHOR_*
+    int gspace;           // GJ_GRAMIAN_*
     int p[2];
     double eps2;
     double alpha[2], q[2], alpha_min[2], lam[2], lo[2], hi[2];
@@ -59,6 +61,7 @@ struct FieldVecs {
     const R *wdep[2];      // nz values
     const R *iwdep[2];     // 1 / wdep, nz values
     const R *whard[2];     // may be null
+    R *mtp[2];             // W_{k-1} m_{k-1} (previous-model anchor only), else null
 };
 
 template <typename R> __device__ __forceinline__ R rsqrt_t(R x);
@@ -111,11 +114,12 @@ struct ProModel {
     SolverDev *S;
     int nx, ny;
     // per-thread
-    int upd, pw[2];
+    int upd, pw[2], gsp;
     R s[2], lo[2], hi[2], eps2;
     R acc[3];
     __device__ void init() {
         upd = S->pending_update;
+        gsp = S->gspace;
         eps2 = (R)S->eps2;
         for (int i = 0; i < 2; ++i) {
             s[i] = (R)S->s[i]; lo[i] = (R)S->lo[i]; hi[i] = (R)S->hi[i]; pw[i] = S->p[i];
@@ -125,20 +129,22 @@ struct ProModel {
     __device__ __forceinline__ void fetch(int la, int lb, bool, int j, R &a, R &b) {
         const size_t c = (size_t)la * nx + j;
         const int r = la / ny;
-        R mv[2];
+        R mv[2], gv[2];
         for (int i = 0; i < 2; ++i) {
             R mi = F.m[i][c];
             if (upd) {
                 const R w = weight(F, i, pw[i], eps2, r, c, mi);
+                if (F.mtp[i]) F.mtp[i][c] = w * mi;  // W_k m_k, the next anchor
                 mi = mi - s[i] * F.p[i][c] / w;
                 mi = fmin(fmax(mi, lo[i]), hi[i]);
                 F.m[i][c] = mi;
             }
             mv[i] = mi;
+            gv[i] = gsp ? weight(F, i, pw[i], eps2, r, c, mi) * mi : mi;  // Gramian space
         }
-        acc[0] += mv[0] * mv[0];
-        acc[1] += mv[1] * mv[1];
-        acc[2] += mv[0] * mv[1];
+        acc[0] += gv[0] * gv[0];
+        acc[1] += gv[1] * gv[1];
+        acc[2] += gv[0] * gv[1];
         a = mv[0];
         b = mv[1];
     }
@@ -161,10 +167,10 @@ struct ProModel {
                 ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c] : R(0);
             }
         }
-        if (upd) {
-            R iwd[2];
+        R wd[2], iwd[2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) iwd[i] = F.iwdep[i][r];
+        for (int i = 0; i < 2; ++i) { wd[i] = F.wdep[i][r]; iwd[i] = F.iwdep[i][r]; }
+        if (upd) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = j0 + k * stride;
@@ -176,6 +182,7 @@ struct ProModel {
                     lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
                     R inv_w = iwl * iwd[i];
                     if (F.whard[i]) inv_w /= wh[i][k];
+                    if (F.mtp[i]) F.mtp[i][c] = wd[i] * wh[i][k] * wl * mv[i][k];  // W_k m_k, the next anchor
                     R mi = mv[i][k] - s[i] * pv[i][k] * inv_w;
                     mi = fmin(fmax(mi, lo[i]), hi[i]);
                     F.m[i][c] = mi;
@@ -185,9 +192,19 @@ struct ProModel {
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            acc[0] += mv[0][k] * mv[0][k];
-            acc[1] += mv[1][k] * mv[1][k];
-            acc[2] += mv[0][k] * mv[1][k];
+            R gv[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                gv[i] = mv[i][k];
+                if (gsp) {  // the Gramian of the weighted models W(m) m
+                    R wl, iwl;
+                    lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
+                    gv[i] = wd[i] * wh[i][k] * wl * mv[i][k];
+                }
+            }
+            acc[0] += gv[0] * gv[0];
+            acc[1] += gv[1] * gv[1];
+            acc[2] += gv[0] * gv[1];
             a[k] = mv[0][k];
             b[k] = mv[1][k];
         }
@@ -303,25 +320,29 @@ struct EpiGradient {
     SolverDev *S;
     int nx, ny;
     R alpha[2], lam[2], eps2, g11, g22, g12;
-    int pw[2];
+    int pw[2], gsp, prev;
     R acc[2];
     __device__ void init() {
         for (int i = 0; i < 2; ++i) { alpha[i] = (R)S->alpha[i]; lam[i] = (R)S->lam[i]; pw[i] = S->p[i]; }
         eps2 = (R)S->eps2;
         g11 = (R)S->G[0]; g22 = (R)S->G[1]; g12 = (R)S->G[2];
+        gsp = S->gspace;
+        prev = S->anchor == GJ_ANCHOR_PREVIOUS && S->k > 0;  // W_{k-1} m_{k-1} exists from k = 1
         acc[0] = acc[1] = 0;
     }
     __device__ __forceinline__ void store(int la, int, bool, int j, R a, R b) {
         const size_t c = (size_t)la * nx + j;
         const int r = la / ny;
-        const R m1 = F.m[0][c], m2 = F.m[1][c];
-        const R lG[2] = {g22 * m1 - g12 * m2, g11 * m2 - g12 * m1};
+        const R mm[2] = {F.m[0][c], F.m[1][c]};
+        const R w[2] = {weight(F, 0, pw[0], eps2, r, c, mm[0]), weight(F, 1, pw[1], eps2, r, c, mm[1])};
+        // ascent directions in the chosen space (RRCG:2-3 or Eq. steepestascenta/b)
+        const R u0 = gsp ? w[0] * mm[0] : mm[0], u1 = gsp ? w[1] * mm[1] : mm[1];
+        const R lG[2] = {g22 * u0 - g12 * u1, g11 * u1 - g12 * u0};
         const R g[2] = {a, b};
-        const R mm[2] = {m1, m2};
         for (int i = 0; i < 2; ++i) {
-            const R w = weight(F, i, pw[i], eps2, r, c, mm[i]);
             const R ma = F.mapr[i] ? F.mapr[i][c] : R(0);
-            const R li = g[i] / w + alpha[i] * (w * mm[i] - w * ma) + lam[i] * lG[i];
+            const R anchor = prev ? F.mtp[i][c] : w[i] * ma;
+            const R li = g[i] / w[i] + alpha[i] * (w[i] * mm[i] - anchor) + lam[i] * lG[i];
             F.l[i][c] = li;
             acc[i] += li * li;
         }
@@ -331,7 +352,7 @@ struct EpiGradient {
                                                 const R (&b)[K]) {
         const size_t c0 = (size_t)la * nx;
         const int r = la / ny;
-        R mv[2][K], wh[2][K], ma[2][K];
+        R mv[2][K], wh[2][K], ma[2][K], an[2][K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -341,6 +362,7 @@ struct EpiGradient {
                 mv[i][k] = ok ? F.m[i][c0 + j] : R(0);
                 wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
                 ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
+                an[i][k] = (ok && prev) ? F.mtp[i][c0 + j] : R(0);
             }
         }
         R wd[2], iwd[2];
@@ -350,15 +372,22 @@ struct EpiGradient {
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
             if (j >= n) continue;
-            const R lG[2] = {g22 * mv[0][k] - g12 * mv[1][k], g11 * mv[1][k] - g12 * mv[0][k]};
-            const R g[2] = {a[k], b[k]};
+            R w[2], inv_w[2];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 R wl, iwl;
                 lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
-                R w = wd[i] * wl, inv_w = iwl * iwd[i];
-                if (F.whard[i]) { w *= wh[i][k]; inv_w /= wh[i][k]; }
-                const R li = g[i] * inv_w + alpha[i] * w * (mv[i][k] - ma[i][k]) + lam[i] * lG[i];
+                w[i] = wd[i] * wl;
+                inv_w[i] = iwl * iwd[i];
+                if (F.whard[i]) { w[i] *= wh[i][k]; inv_w[i] /= wh[i][k]; }
+            }
+            const R u0 = gsp ? w[0] * mv[0][k] : mv[0][k], u1 = gsp ? w[1] * mv[1][k] : mv[1][k];
+            const R lG[2] = {g22 * u0 - g12 * u1, g11 * u1 - g12 * u0};
+            const R g[2] = {a[k], b[k]};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const R anchor = prev ? an[i][k] : w[i] * ma[i][k];
+                const R li = g[i] * inv_w[i] + alpha[i] * (w[i] * mv[i][k] - anchor) + lam[i] * lG[i];
                 F.l[i][c0 + j] = li;
                 acc[i] += li * li;
             }
@@ -570,6 +599,7 @@ struct gj_rrcg {
     SolverDev *S = nullptr;   // device
     void *buf = nullptr;      // p, l (2 fields each, n), v (2 x s), wd (2 x s)
     const void *dobs[2], *mapr[2], *wdep[2], *whard[2];
+    bool prev_anchor = false;
     void *m[2];
     gj_rrcg_hist *hist = nullptr;
     cudaGraph_t graph = nullptr;
@@ -642,6 +672,7 @@ struct SolverLaunch {
             F.mapr[i] = static_cast<const R *>(sv->mapr[i]);
             F.wdep[i] = static_cast<const R *>(sv->wdep[i]);
             F.iwdep[i] = b + (size_t)4 * n + (size_t)4 * s + (size_t)i * o->nz;
+            F.mtp[i] = sv->prev_anchor ? b + (size_t)4 * n + (size_t)4 * s + (size_t)2 * o->nz + (size_t)i * n : nullptr;
             F.whard[i] = static_cast<const R *>(sv->whard[i]);
         }
     }
@@ -825,6 +856,12 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
     if (P->kmax < 0) { set_error("gj_rrcg_create: kmax must be >= 0"); return GJ_ERR_ARG; }
     if (!(P->eps2 > 0)) { set_error("gj_rrcg_create: eps2 must be > 0"); return GJ_ERR_ARG; }
     if (P->scalars < 0 || P->scalars > 2) { set_error("gj_rrcg_create: bad scalars mode"); return GJ_ERR_ARG; }
+    if (P->anchor != GJ_ANCHOR_APRIORI && P->anchor != GJ_ANCHOR_PREVIOUS) {
+        set_error("gj_rrcg_create: bad anchor"); return GJ_ERR_ARG;
+    }
+    if (P->gramian_space != GJ_GRAMIAN_ORIGINAL && P->gramian_space != GJ_GRAMIAN_WEIGHTED) {
+        set_error("gj_rrcg_create: bad gramian_space"); return GJ_ERR_ARG;
+    }
     gj_rrcg *sv = new (std::nothrow) gj_rrcg();
     if (!sv) { set_error("gj_rrcg_create: host allocation failed"); return GJ_ERR_OOM; }
     const gj_op *o = ops[0];
@@ -838,12 +875,14 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
         sv->m[i] = m[i];
     }
     sv->hist = hist;
+    sv->prev_anchor = P->anchor == GJ_ANCHOR_PREVIOUS;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t es = elem_bytes(o->prec);
     const size_t n = (size_t)o->nx * o->ny * o->nz, s = (size_t)o->sx * o->sy;
     cudaError_t e;
     if ((e = cudaMalloc(&sv->S, sizeof(SolverDev))) != cudaSuccess) { delete sv; return cuda_fail(e, "solver state"); }
-    if ((e = cudaMalloc(&sv->buf, (4 * n + 4 * s + 2 * (size_t)o->nz) * es)) != cudaSuccess) {
+    const size_t nbuf = 4 * n + 4 * s + 2 * (size_t)o->nz + (sv->prev_anchor ? 2 * n : 0);
+    if ((e = cudaMalloc(&sv->buf, nbuf * es)) != cudaSuccess) {
         cudaFree(sv->S); delete sv; return cuda_fail(e, "solver vectors");
     }
     SolverDev h{};
@@ -851,6 +890,8 @@ extern "C" gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_par
     h.stop_on_chi2 = P->stop_on_chi2;
     const bool lam0 = P->lambda[0] == 0 && P->lambda[1] == 0;
     h.per_field = P->scalars == GJ_SCALARS_PER_FIELD || (P->scalars == GJ_SCALARS_AUTO && lam0);
+    h.anchor = P->anchor;
+    h.gspace = P->gramian_space;
     h.eps2 = P->eps2;
     for (int i = 0; i < 2; ++i) {
         h.p[i] = P->p[i];

@@ -56,7 +56,8 @@ KW = dict(p=(1, 1), alpha1=(2e4, 2e4), q=(0.95, 0.95), lam=(50.0, 1500.0), lo=(0
 def oracle_params(kw):
     return RRCGParams(p=kw["p"], alpha1=kw["alpha1"], q=kw["q"], alpha_min=kw.get("alpha_min", (0.0, 0.0)),
                       lam=kw["lam"], lo=kw["lo"], hi=kw["hi"], kmax=kw["kmax"], stop_on_chi2=kw["stop_on_chi2"],
-                      scalars=kw.get("scalars", "auto"))
+                      scalars=kw.get("scalars", "auto"), anchor=kw.get("anchor", "apriori"),
+                      gramian_space=kw.get("gramian_space", "original"))
 
 
 @pytest.fixture(scope="module")
@@ -97,7 +98,8 @@ def test_joint_fp32_mixed_within_model_tolerance(small):
         assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
 
 
-@pytest.mark.parametrize("variant", ["per_field_lam0", "p2_joint", "alpha_floor_stop"])
+@pytest.mark.parametrize("variant", ["per_field_lam0", "p2_joint", "alpha_floor_stop", "weighted_gramian",
+                                     "previous_anchor"])
 def test_solver_variants_fp64(small, variant):
     gj = lib()
     w, g, A, dob, sig, wdep = small
@@ -106,6 +108,10 @@ def test_solver_variants_fp64(small, variant):
         kw.update(lam=(0.0, 0.0), kmax=30)
     elif variant == "p2_joint":
         kw.update(p=(2, 2), lam=(50.0, 8e5), alpha1=(2e4, 4e4), alpha_min=(50.0, 50.0), kmax=40)
+    elif variant == "weighted_gramian":  # Sec. 3.1.4: Eq. steepestascenta/b on W m
+        kw.update(lam=(5000.0, 10000.0), gramian_space="weighted", kmax=40)
+    elif variant == "previous_anchor":  # RRCG:4 with the printed m~_k - m~_{k-1}
+        kw.update(anchor="previous", kmax=30)
     else:
         kw.update(alpha_min=(500.0, 900.0), q=(0.8, 0.85), kmax=150, stop_on_chi2=True)
     ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw))
