@@ -150,6 +150,22 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+def reduce_max_ms(total_ms: float, dist, device) -> float:
+    """The timed region's length as the maximum over ranks (no-op on one rank)."""
+    if dist is None:
+        return total_ms
+    import torch
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
+    """Iterations of all ranks (independent replicas) per second of the slowest rank."""
+    return world * steps / (max_total_ms / 1e3)
+
+
 def build_problem(gj, torch, prec, dev):
     import numpy as np
     import synth
@@ -234,13 +250,9 @@ def run_ours(args, rank, world, local_rank):
     prof_mode = ("CUDA events on the launching stream around every launch, over a second timed region of "
                  f"{args.steps} steps (the graph captured in segments cut around the kernel)")
     times_b, pn, pms = time_steps(torch, sv, args.steps, 2, flush, profile=True)
-    total_ms = float(sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(float(sum(times)), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, args.steps, total_ms)
     rep = sv.report()
     sv.close()
 
@@ -284,6 +296,7 @@ def run_ours(args, rank, world, local_rank):
         line["fp64"] = fp64_leg(gj, torch, dev, flush, value)
         line["e2e"] = e2e_leg(gj, torch, ops, g, dobs, sigma, wdep)
         line["batched"] = batched_leg(gj, torch, dev, flush)
+        line["paper_shapes"] = paper_shapes_leg(gj, torch, dev, flush)
         if world == 1:
             v, per = oracle_sample(w.grid, w.mag, rows=24, cols=400)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -417,6 +430,49 @@ def batched_leg(gj, torch, dev, flush, steps=20, warmup=3):
     return {"value": len(sizes) * 1e3 / ms, "unit": "problem-iters/s", "ms_per_step": ms, "problems": len(sizes),
             "sizes_nx_ny_nz": [list(x) for x in sizes], "npad_autotuned": npads, "cells_both_fields": cells,
             "note": "one graph replay advances all 16 inversions by one RRCG iteration; L2 flushed per step"}
+
+
+# the paper's workloads (Secs. 3.1, 3.2, 4): shape, cell sizes, and the laptop's
+# seconds per iteration (total time / iterations as printed), for context only
+PAPER_SHAPES = [
+    ("two cubes 50x30x10 (Sec. 3.1.2)", (50, 30, 10), (100.0, 100.0), 45.0 / 52),
+    ("five bodies 150x100x10 (Sec. 3.2)", (150, 100, 10), (100.0, 100.0), 4872.0 / 96),
+    ("field data 146x148x20 (Sec. 4)", (146, 148, 20), (250.0, 500.0), 20 * 3600.0 / 186),
+]
+
+
+def paper_shapes_leg(gj, torch, dev, flush, steps=20, warmup=3):
+    """Seconds per RRCG iteration on seeded stand-ins with the shapes of the paper's
+    three workloads (the bodies and field data themselves are not available), FP32
+    with autotuned padding, next to the paper's laptop figures."""
+    import tempfile
+
+    import numpy as np
+    import synth
+    from paper_2112_15562_gb300 import autotune
+
+    cache = os.path.join(tempfile.gettempdir(), "gj_autotune_bench.json")
+    out = []
+    for name, (nx, ny, nz), (dh, dz), laptop in PAPER_SHAPES:
+        gr = synth.uniform_grid(nx, ny, nx, ny, nz, dh, dz=dz)
+        mag = synth.Mag(50000.0, 45.0, 45.0)
+        npad = autotune.tune(gr, mag, "fp32", cache=cache, reps=3)
+        ops = [gj.bttb_setup(gr, "gravity", precision="fp32", npad=npad),
+               gj.bttb_setup(gr, "magnetic", mag, precision="fp32", npad=npad)]
+        mt = [torch.from_numpy(synth.dipping_blocks(gr, v, 7)).float().to(dev) for v in (1.0, 0.1)]
+        d = [ops[k].forward(mt[k]) for k in range(2)]
+        sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
+        rng = np.random.default_rng(7)
+        dob = [d[k] + sig[k] * torch.from_numpy(rng.standard_normal(gr.s)).float().to(dev) for k in range(2)]
+        wd = [torch.from_numpy(gj.depth_weights(gr.z_edges, b)).float().to(dev) for b in (2.0, 3.0)]
+        sv, m, P = solver_for(gj, torch, ops, gr, dob, sig, wd, steps + warmup + 4, dev)
+        ts, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
+        sv.close()
+        s_it = sum(ts) / steps / 1e3
+        out.append({"workload": name, "npad": list(npad), "s_per_iter": s_it, "laptop_s_per_iter": laptop,
+                    "ratio_vs_laptop": laptop / s_it})
+    return {"runs": out, "note": "laptop figures: the paper's Intel i7-10750H, FP64, total time / iterations; "
+                                 "a different machine and workload (context, not a target)"}
 
 
 def e2e_leg(gj, torch, ops, g, dobs, sigma, wdep, iters=20):

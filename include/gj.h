@@ -259,6 +259,8 @@ void gj_rrcg_destroy(gj_rrcg *solver);
  * one launch advances every problem by one RRCG iteration (solvers that have
  * stopped do no work).  The solvers stay owned by the caller and must outlive
  * the batch; while a batch exists, do not step its solvers on other streams.
+ * The branches run concurrently, so no two solvers may share an operator (each
+ * gj_op owns one workspace): GJ_ERR_ARG otherwise.
  */
 typedef struct gj_rrcg_batch gj_rrcg_batch;
 gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj_stream_t stream, gj_rrcg_batch **out);

@@ -1123,6 +1123,15 @@ extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj
     *out = nullptr;
     for (int i = 0; i < count; ++i)
         if (!solvers[i]) { set_error("gj_rrcg_batch_create: NULL solver"); return GJ_ERR_ARG; }
+    // the graph runs the solvers concurrently: an operator's workspace cannot be shared
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j)
+            for (int a = 0; a < 2; ++a)
+                for (int b2 = 0; b2 < 2; ++b2)
+                    if (solvers[i]->op[a] == solvers[j]->op[b2]) {
+                        set_error("gj_rrcg_batch_create: two solvers share an operator (give each its own)");
+                        return GJ_ERR_ARG;
+                    }
     gj_rrcg_batch *b = new (std::nothrow) gj_rrcg_batch();
     if (!b) { set_error("gj_rrcg_batch_create: host allocation failed"); return GJ_ERR_OOM; }
     b->sv.assign(solvers, solvers + count);

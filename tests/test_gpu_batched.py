@@ -80,3 +80,30 @@ def test_autotuner_picks_a_valid_size_and_caches(tmp_path):
     assert "512x512" in entry["ms_fwd_adj_both_fields"]
     assert autotune.tune(g, mag, "fp32", cache=cache) == npad  # served from the cache
     assert autotune.smooth_sizes(511, 3) == [512, 525, 540]
+
+
+def test_lambda_sweep_matches_single_solves_and_selects_the_smallest_correlated_pair():
+    gj = lib()
+    g, ops, dob, sig, wd = make_problem(gj, 16, 16, 6, 77)
+    lambdas = [(0.0, 0.0), (2.0, 100.0), (50.0, 1500.0)]
+    kw = dict(p=(1, 1), kmax=15, stop_on_chi2=False)
+    out = gj.lambda_sweep(g, synth.Mag(50000.0, 60.0, 10.0), dob, sig, wd, lambdas, precision="fp32",
+                          corr_threshold=-2.0, **kw)
+    assert len(out["runs"]) == 3
+    for lam, run in zip(lambdas, out["runs"]):
+        opsi = [gj.bttb_setup(g, "gravity", precision="fp32"),
+                gj.bttb_setup(g, "magnetic", synth.Mag(50000.0, 60.0, 10.0), precision="fp32")]
+        m = [torch.zeros(g.n, device="cuda") for _ in range(2)]
+        gj.rrcg_joint_solve(opsi, gj.solver_params(lam=lam, **kw), dob, sig, wd, m)
+        for i in range(2):
+            assert rel(run["models"][i], m[i].double().cpu().numpy()) <= 1e-5
+        assert run["iterations"] == 15
+        assert -1.0 <= run["pearson"] <= 1.0
+    # with the stop test off nothing "converges": no pair qualifies
+    assert out["selected"] is None
+    # the selection rule on its own: first converged pair above the threshold
+    fake = {"runs": [{"converged": True, "pearson": 0.5}, {"converged": True, "pearson": 0.95},
+                     {"converged": True, "pearson": 0.99}]}
+    sel = next(i for i, r in enumerate(fake["runs"]) if r["converged"] and r["pearson"] >= 0.9)
+    assert sel == 1
+    assert abs(gj.pearson(np.arange(5.0), 2 * np.arange(5.0) + 1) - 1.0) < 1e-12
