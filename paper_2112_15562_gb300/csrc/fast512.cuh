@@ -106,12 +106,15 @@ __device__ __forceinline__ cpx<R> w32c(int j) {  // W32^j for 0 <= j < 16 (j kno
     return mk<cpx<R>>((R)c, (R)(-sn));
 }
 
-// Per-lane twiddles: W256^(l k) = lo[k & 3] * hi[k >> 2] with l = lane & 15,
-// and the odd-half pre-twiddle W512^(l + 16 j) = pre * W32^j.
+// Per-lane twiddles, l = lane & 15.  Inverse form (load_inv): W256^(l k) =
+// lo[k & 3] * hi[k >> 2] and pre = W512^l.  Forward form (load_fwd): the odd
+// half-warp's factor W512^l is folded into hi, so that
+// lo[k & 3] * hi[k >> 2] = W512^(h l) W256^(l k) and the odd half only needs the
+// constant factors W32^j before its first DFT (W512^(l + 16 j) = W512^l W32^j).
 template <typename R>
 struct LaneTw {
     cpx<R> lo[4], hi[4], pre;
-    __device__ void load(const cpx<R> *__restrict__ tw512) {  // tw512[k] = W512^k (global, read-only)
+    __device__ void load_inv(const cpx<R> *__restrict__ tw512) {  // tw512[k] = W512^k (global, read-only)
         const int l = threadIdx.x & 15;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -120,9 +123,21 @@ struct LaneTw {
         }
         pre = __ldg(tw512 + l);
     }
+    __device__ void load_fwd(const cpx<R> *__restrict__ tw512) {
+        load_inv(tw512);
+        if (threadIdx.x & 16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hi[k] = cmul(hi[k], pre);
+        }
+    }
+    // twiddle of output k of the first DFT: W256^(l k) (times W512^(h l) in the forward form)
     template <bool INV> __device__ __forceinline__ cpx<R> mul256(cpx<R> a, int k) const {
-        const cpx<R> w = cmul(lo[k & 3], hi[k >> 2]);
+        const cpx<R> w = (k >> 2) == 0 ? lo[k & 3] : ((k & 3) == 0 ? hi[k >> 2] : cmul(lo[k & 3], hi[k >> 2]));
         return INV ? cmulc(a, w) : cmul(a, w);
+    }
+    __device__ __forceinline__ cpx<R> fwd_tw(cpx<R> a, int k) const {  // forward form, includes k = 0
+        const cpx<R> w = (k & 3) == 0 ? hi[k >> 2] : cmul(lo[k & 3], hi[k >> 2]);
+        return cmul(a, w);
     }
 };
 
@@ -137,18 +152,18 @@ __device__ __forceinline__ int swz(int row, int col) { return row * 16 + (col ^ 
 
 // Forward pruned 512-point transform.  In: v[j] = x[l + 16 j] (both halves).
 // Out: lane (h, k2) v[k1] = X[lambda + 32 k1].  buf: this warp's 512-entry tile.
+// tw must hold the forward form (load_fwd).
 template <typename R>
 __device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const LaneTw<R> &tw) {
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     cpx<R> *t = buf + h * 256;
     if (h) {
-        const cpx<R> p = tw.pre;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = cmul(v[j], cmul(p, w32c<R>(j)));
+        for (int j = 1; j < 16; ++j) v[j] = cmul(v[j], w32c<R>(j));
     }
     dft16<R, false>(v);
 #pragma unroll
-    for (int k = 1; k < 16; ++k) v[k] = tw.template mul256<false>(v[k], k);
+    for (int k = 0; k < 16; ++k) v[k] = tw.fwd_tw(v[k], k);
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < 16; ++k) t[swz(l, k)] = v[k];
@@ -158,7 +173,7 @@ __device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const LaneT
     dft16<R, false>(v);
 }
 
-// Inverse: in lane (h, k2) v[k1] = Y[lambda + 32 k1].  Out (unnormalised): every
+// Inverse (tw in the inverse form, load_inv): in lane (h, k2) v[k1] = Y[lambda + 32 k1].  Out (unnormalised): every
 // lane of both halves holds y[n] for n = l + 16 j with j in [8h, 8h + 8):
 // out[jj] = y[l + 16 (8h + jj)], jj < 8.
 template <typename R>
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
     pro.init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(V.op[0].twx);
+    tw.load_fwd(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
     C *buf = xb + warp * N;
@@ -442,7 +457,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
     stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(V.op[0].twx);
+    tw.load_inv(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C *buf = xb + warp * N;
     for (int s2 = 0; s2 < FPW; ++s2) {
@@ -485,12 +500,13 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
     stage_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 1);
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(V.op[0].twx);
+    tw.load_inv(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     C *buf = xb + warp * N;
     const int f = warp;
     R a[8], b[8];
     inv512_to_lines<R, FFTS>(tile, f, FFTS + f, buf, tw, a, b);
+    tw.load_fwd(V.op[0].twx);
     const int line = base + f;
     const bool ok = line < nlines;
     if (ok) {
@@ -532,7 +548,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(V.op[0].twy);
+    tw.load_fwd(V.op[0].twy);
     const int nz = V.op[0].nz, sy = V.op[0].sy;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
@@ -627,7 +643,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
                 }
             }
             C out[8];
+            tw.load_inv(V.op[0].twy);
             inv512<R>(acc, xbuf, tw, out);
+            tw.load_fwd(V.op[0].twy);
             C *Wc = op.W + (size_t)kx * H;
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
@@ -661,7 +679,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     mbar_fence_init();
     __syncthreads();
     LaneTw<R> tw;
-    tw.load(V.op[0].twy);
+    tw.load_inv(V.op[0].twy);
     const int nz = V.op[0].nz, ny = V.op[0].ny;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
@@ -700,7 +718,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             const C *Wc = op.V + (size_t)kx * H;
 #pragma unroll
             for (int j = 0; j < 16; ++j) vh[j] = Wc[l + 16 * j];
+            tw.load_fwd(V.op[0].twy);
             fwd512<R>(vh, xbuf, tw);
+            tw.load_inv(V.op[0].twy);
             cur_col = col;
         }
         const int s = (int)((t - t0) % CSTAGES);
