@@ -480,6 +480,203 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
     epi.flush(red);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent joint row passes (both fields in one complex transform per line).
+// Each warp takes a balanced contiguous range of the lines, so that no warp waits
+// on another and no launch ends in a partial wave.  The half spectra of up to G
+// consecutive lines of one layer sit in the warp's own staging tile
+// stage[field][kx][P] (P = G + 1, odd: conflict-free by column and by slot) and
+// move to or from the transposed layout out[r][kx][iy] in runs of G lines.
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Z = FFT(a + i b) in the lane layout (v[k1] = Z[lambda + 32 k1]) -> the half
+// spectra A = (Z[kx] + conj Z[N - kx]) / 2 and B = (Z[kx] - conj Z[N - kx]) / 2i,
+// kx = 0..256, into slot g of the staging tile.  For lambda != 0, Z[N - kx] sits in
+// lane (h, 16 - l - h) at k1' = 15 - k1; lane 0 (lambda = 0) holds it at 16 - k1.
+template <typename R, int P>
+__device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *stage, int g) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    const int partner = h ? 31 - l : ((16 - l) & 15);
+    C *sa = stage, *sb = stage + NC * P;
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        C zm;
+        zm.x = __shfl_sync(0xffffffffu, v[15 - k1].x, partner);
+        zm.y = __shfl_sync(0xffffffffu, v[15 - k1].y, partner);
+        if (lane == 0) zm = v[(16 - k1) & 15];
+        const C zk = v[k1];
+        const int kx = lam + 32 * k1;
+        sa[kx * P + g] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        sb[kx * P + g] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    }
+    if (lane == 0) {  // kx = 256 is its own partner
+        sa[H * P + g] = mk<C>(v[8].x, R(0));
+        sb[H * P + g] = mk<C>(v[8].y, R(0));
+    }
+}
+
+// Slots [gs, ge] of the staging tile -> oa[kx * H + g], ob[kx * H + g] (runs of G).
+template <typename R, int G>
+__device__ __forceinline__ void stage_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int gs, int ge) {
+    static_assert(32 % G == 0, "G must divide the warp");
+    constexpr int P = G + 1, KX = 32 / G;
+    const int lane = threadIdx.x & 31, g = lane % G;
+    if (g < gs || g > ge) return;
+    for (int kx = lane / G; kx < NC; kx += KX) {
+        oa[(size_t)kx * H + g] = stage[kx * P + g];
+        ob[(size_t)kx * H + g] = stage[(NC + kx) * P + g];
+    }
+}
+
+// ia[kx * H + g], ib[kx * H + g] -> slots [gs, ge] of the staging tile (asynchronous
+// copies; cp_async_wait_all and a warp barrier make them visible).
+template <typename R, int G>
+__device__ __forceinline__ void stage_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int gs, int ge) {
+    constexpr int P = G + 1, KX = 32 / G;
+    const int lane = threadIdx.x & 31, g = lane % G;
+    if (g < gs || g > ge) return;
+    for (int kx = lane / G; kx < NC; kx += KX) {
+        cp_async8(stage + kx * P + g, ia + (size_t)kx * H + g);
+        cp_async8(stage + (NC + kx) * P + g, ib + (size_t)kx * H + g);
+    }
+}
+
+// Slot g of the staging tile (A + i B, Hermitian-extended) -> inverse transform ->
+// y[lane + 32 i] in a[i] + i b[i].
+template <typename R, int P>
+__device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const LaneTw<R> &tw,
+                                               R (&a)[8], R (&b)[8]) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    C v[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+        const int k = lam + 32 * k1;
+        const bool lo = k <= H;
+        const int kk = lo ? k : N - k;
+        C A = stage[kk * P + g], B = stage[(NC + kk) * P + g];
+        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+        v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+    }
+    C out[8];
+    inv512<R>(v, buf, tw, out);
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const C y = buf[lane + 32 * i];
+        a[i] = y.x;
+        b[i] = y.y;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> *sel_buf(const OpView<R> &o, int sel) {  // 0 = Z, 1 = W, 2 = V
+    return sel == 0 ? o.Z : (sel == 1 ? o.W : o.V);
+}
+
+// Forward joint row pass: line t of both fields (through the prologue functor) ->
+// half spectra out[r][kx][iy], t = r lpl + iy.
+template <typename R, class Pro, int NW, int G>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512w(View2<R> V, int nlines, int lpl, int n_in, int out_sel,
+                                                            Pro pro, const int *done) {
+    using C = cpx<R>;
+    constexpr int P = G + 1;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (N + 2 * NC * P);
+    C *stage = buf + N;
+    __shared__ double red[128];
+    pro.init();
+    LaneTw<R> tw;
+    tw.load_fwd(V.op[0].twx);
+    const long long Wt = seg_warps((long long)gridDim.x * NW, nlines);
+    const long long w = (long long)blockIdx.x * NW + warp;
+    if (w < Wt) {
+        const int t0 = (int)seg_begin(w, nlines, Wt), t1 = (int)seg_begin(w + 1, nlines, Wt);
+        C *out0 = sel_buf(V.op[0], out_sel), *out1 = sel_buf(V.op[1], out_sel);
+        int gs = -1;
+        for (int t = t0; t < t1; ++t) {
+            const int r = t / lpl, iy = t - r * lpl, g = iy % G;
+            if (gs < 0) gs = g;
+            R a[8], b[8];
+            {
+                R a0[4], b0[4], a1[4], b1[4];
+                pro.template fetch_batch<4>(t, t, true, lane, 32, n_in, a0, b0);
+                pro.template fetch_batch<4>(t, t, true, lane + 128, 32, n_in, a1, b1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
+            }
+            C v[16];
+            fwd512_from_lines<R>(a, b, buf, tw, v);
+            split_to_stage<R, P>(v, stage, g);
+            if (g == G - 1 || t == t1 - 1 || iy == lpl - 1) {
+                __syncwarp();
+                const size_t off = (size_t)r * NC * H + (iy - g);
+                stage_store<R, G>(stage, out0 + off, out1 + off, gs, g);
+                __syncwarp();
+                gs = -1;
+            }
+        }
+    }
+    pro.flush(red);
+}
+
+// Inverse joint row pass: half spectra in[r][kx][iy] -> line t of both fields,
+// cropped to n_out, through the epilogue functor.
+template <typename R, class Epi, int NW, int G>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_inv512w(View2<R> V, int nlines, int lpl, int n_out, int in_sel,
+                                                            Epi epi, const int *done) {
+    using C = cpx<R>;
+    constexpr int P = G + 1;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (N + 2 * NC * P);
+    C *stage = buf + N;
+    __shared__ double red[128];
+    epi.init();
+    LaneTw<R> tw;
+    tw.load_inv(V.op[0].twx);
+    const long long Wt = seg_warps((long long)gridDim.x * NW, nlines);
+    const long long w = (long long)blockIdx.x * NW + warp;
+    if (w < Wt) {
+        const int t0 = (int)seg_begin(w, nlines, Wt), t1 = (int)seg_begin(w + 1, nlines, Wt);
+        const C *in0 = sel_buf(V.op[0], in_sel), *in1 = sel_buf(V.op[1], in_sel);
+        for (int t = t0; t < t1; ++t) {
+            const int r = t / lpl, iy = t - r * lpl, g = iy % G;
+            if (t == t0 || g == 0) {  // a new run: slots g .. end of block, range or layer
+                const int ge = g + min(G - 1 - g, min(t1 - 1 - t, lpl - 1 - iy));
+                const size_t off = (size_t)r * NC * H + (iy - g);
+                __syncwarp();
+                stage_load<R, G>(stage, in0 + off, in1 + off, g, ge);
+                cp_async_wait_all();
+                __syncwarp();
+            }
+            R a[8], b[8];
+            stage_to_lines<R, P>(stage, g, buf, tw, a, b);
+            R a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
+            epi.template store_batch<4>(t, t, true, lane, 32, n_out, a0, b0);
+            epi.template store_batch<4>(t, t, true, lane + 128, 32, n_out, a1, b1);
+        }
+    }
+    epi.flush(red);
+}
+
 // Fused data-line pass of the solver: for station row jy of both fields, inverse
 // row transform of W (the cropped forward product), the residual epilogue
 // (r~ = W_d (A m - d), v = W_d r~, Phi partials), then the forward row transform
@@ -763,6 +960,9 @@ template <typename R, int NW, int FPW> inline size_t smem_row_inv() {
 template <typename R, int NW> inline size_t smem_row_resid() {
     const size_t t = (size_t)NC * (2 * NW + 1) > (size_t)NW * (N + 1) ? (size_t)NC * (2 * NW + 1) : (size_t)NW * (N + 1);
     return (t + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW, int G> inline size_t smem_row_w() {
+    return (size_t)NW * (N + 2 * NC * (G + 1)) * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_fwd() {
     return (size_t)CWARPS * (CSTAGES * (H + N) + N) * sizeof(cpx<R>);

@@ -685,10 +685,10 @@ struct SolverLaunch {
         cudaFuncGetAttributes(&fa, k_scalars_after_residual);
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
-            set_row_fwd_attr<R, ProModel<R>, kCellNW, kCellFPW>();
-            set_row_fwd_attr<R, ProDirection<R>, kCellNW, kCellFPW>();
+            set_row_fwd_w_attr<R, ProModel<R>>();
+            set_row_fwd_w_attr<R, ProDirection<R>>();
             set_row_resid_attr<R, EpiResidual<R>, kDataNW>();
-            set_row_inv_attr<R, EpiGradient<R>, kCellNW, kCellFPW>();
+            set_row_inv_w_attr<R, EpiGradient<R>>();
             set_row_inv_attr<R, EpiQNorm<R>, kDataNW, kDataFPW>();
             set_col_attr<R>();
             return;
@@ -748,7 +748,7 @@ struct SolverLaunch {
         if constexpr (std::is_same_v<R, float>) if (fast) {
             ProModel<R> pm{F, sv->S, o->nx, o->ny};
             using namespace f512;
-            row_fwd<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
+            row_fwd_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
             forward_columns(st);
             // residual, Phi and the residual rows' spectra for the adjoint, in one pass
             EpiResidual<R> er{F, sv->S, o->sx};
@@ -773,9 +773,9 @@ struct SolverLaunch {
             using namespace f512;
             col_adj<R>(V2, o->col_grid, done, st);
             EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
-            row_inv<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
+            row_inv_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
             ProDirection<R> pd{F, sv->S, o->nx, o->ny};
-            row_fwd<R, kCellNW, kCellFPW>(V2, 1, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
+            row_fwd_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
             row_inv<R, kDataNW, kDataFPW>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
