@@ -482,30 +482,51 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
 
 // ---------------------------------------------------------------------------
 // Persistent joint row passes (both fields in one complex transform per line).
-// Each warp takes a balanced contiguous range of the lines, so that no warp waits
-// on another and no launch ends in a partial wave.  The half spectra of up to G
-// consecutive lines of one layer sit in the warp's own staging tile
-// stage[field][kx][P] (P = G + 1, odd: conflict-free by column and by slot) and
-// move to or from the transposed layout out[r][kx][iy] in runs of G lines.
+// A team of four warps takes a balanced contiguous range of the aligned four-line
+// groups of the layers (warp k of the team transforms line 4q + k of group q), so
+// that no launch ends in a partial wave.  The half spectra of a group sit in a
+// double-buffered team tile stage[field][slot][kq(kx)] and move to or from the
+// transposed layout out[r][kx][iy] as whole 32-byte sectors (four lines of one
+// column).  kq puts even columns first and odd ones from 136 on; with the slot
+// stride LS = 274 (2 mod 16), a half-warp's 16 consecutive columns of one line, and
+// its 4 x 4 (column, slot) pairs of a group, each fall in 16 distinct bank pairs.
+// One named barrier per group and team.  The rows the functor reads in every
+// launch (m, p, l) are staged one line ahead with asynchronous copies.
 
+constexpr int TEAM = 4;                 // warps per team = lines per group
+constexpr int LS = 274, FS = TEAM * LS;  // slot and field strides of a team tile (complex words)
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {  // at most NPEND of the newest groups still in flight
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+__device__ __forceinline__ void team_barrier(int team) {  // barrier 0 stays with __syncthreads
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + team), "r"(TEAM * 32) : "memory");
+}
+
+__device__ __forceinline__ int kq(int kx) { return (kx & 1) ? 136 + (kx >> 1) : (kx >> 1); }
 
 // Z = FFT(a + i b) in the lane layout (v[k1] = Z[lambda + 32 k1]) -> the half
 // spectra A = (Z[kx] + conj Z[N - kx]) / 2 and B = (Z[kx] - conj Z[N - kx]) / 2i,
-// kx = 0..256, into slot g of the staging tile.  For lambda != 0, Z[N - kx] sits in
+// kx = 0..256, into slot g of a team tile.  For lambda != 0, Z[N - kx] sits in
 // lane (h, 16 - l - h) at k1' = 15 - k1; lane 0 (lambda = 0) holds it at 16 - k1.
-template <typename R, int P>
+template <typename R>
 __device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *stage, int g) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
-    const int lam = 2 * l + h;
     const int partner = h ? 31 - l : ((16 - l) & 15);
-    C *sa = stage, *sb = stage + NC * P;
+    C *sa = stage + g * LS, *sb = sa + FS;
+    const int q0 = h * 136 + l;  // kq(lambda + 32 k1) = q0 + 16 k1
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) {
         C zm;
@@ -513,57 +534,56 @@ __device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *st
         zm.y = __shfl_sync(0xffffffffu, v[15 - k1].y, partner);
         if (lane == 0) zm = v[(16 - k1) & 15];
         const C zk = v[k1];
-        const int kx = lam + 32 * k1;
-        sa[kx * P + g] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-        sb[kx * P + g] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        sa[q0 + 16 * k1] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        sb[q0 + 16 * k1] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     }
     if (lane == 0) {  // kx = 256 is its own partner
-        sa[H * P + g] = mk<C>(v[8].x, R(0));
-        sb[H * P + g] = mk<C>(v[8].y, R(0));
+        sa[kq(H)] = mk<C>(v[8].x, R(0));
+        sb[kq(H)] = mk<C>(v[8].y, R(0));
     }
 }
 
-// Slots [gs, ge] of the staging tile -> oa[kx * H + g], ob[kx * H + g] (runs of G).
-template <typename R, int G>
-__device__ __forceinline__ void stage_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int gs, int ge) {
-    static_assert(32 % G == 0, "G must divide the warp");
-    constexpr int P = G + 1, KX = 32 / G;
-    const int lane = threadIdx.x & 31, g = lane % G;
-    if (g < gs || g > ge) return;
-    for (int kx = lane / G; kx < NC; kx += KX) {
-        oa[(size_t)kx * H + g] = stage[kx * P + g];
-        ob[(size_t)kx * H + g] = stage[(NC + kx) * P + g];
+// Slot g < ng of a team tile -> oa[kx * H + g], ob[kx * H + g]; the team's 128
+// threads each take (g, kx) = (tid % 4, tid / 4 + 32 i).
+template <typename R>
+__device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid) {
+    const int g = tid % TEAM;
+    if (g >= ng) return;
+    const cpx<R> *sa = stage + g * LS, *sb = sa + FS;
+    for (int kx = tid / TEAM; kx < NC; kx += 32) {
+        oa[(size_t)kx * H + g] = sa[kq(kx)];
+        ob[(size_t)kx * H + g] = sb[kq(kx)];
     }
 }
 
-// ia[kx * H + g], ib[kx * H + g] -> slots [gs, ge] of the staging tile (asynchronous
-// copies; cp_async_wait_all and a warp barrier make them visible).
-template <typename R, int G>
-__device__ __forceinline__ void stage_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int gs, int ge) {
-    constexpr int P = G + 1, KX = 32 / G;
-    const int lane = threadIdx.x & 31, g = lane % G;
-    if (g < gs || g > ge) return;
-    for (int kx = lane / G; kx < NC; kx += KX) {
-        cp_async8(stage + kx * P + g, ia + (size_t)kx * H + g);
-        cp_async8(stage + (NC + kx) * P + g, ib + (size_t)kx * H + g);
+// ia[kx * H + g], ib[kx * H + g] -> slot g < ng of a team tile (asynchronous copies).
+template <typename R>
+__device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid) {
+    const int g = tid % TEAM;
+    if (g >= ng) return;
+    cpx<R> *sa = stage + g * LS, *sb = sa + FS;
+    for (int kx = tid / TEAM; kx < NC; kx += 32) {
+        cp_async8(sa + kq(kx), ia + (size_t)kx * H + g);
+        cp_async8(sb + kq(kx), ib + (size_t)kx * H + g);
     }
 }
 
-// Slot g of the staging tile (A + i B, Hermitian-extended) -> inverse transform ->
+// Slot g of a team tile (A + i B, Hermitian-extended) -> inverse transform ->
 // y[lane + 32 i] in a[i] + i b[i].
-template <typename R, int P>
+template <typename R>
 __device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const LaneTw<R> &tw,
                                                R (&a)[8], R (&b)[8]) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int lam = 2 * l + h;
+    const C *sa = stage + g * LS, *sb = sa + FS;
     C v[16];
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) {
         const int k = lam + 32 * k1;
         const bool lo = k <= H;
         const int kk = lo ? k : N - k;
-        C A = stage[kk * P + g], B = stage[(NC + kk) * P + g];
+        C A = sa[kq(kk)], B = sb[kq(kk)];
         if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
         v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
     }
@@ -581,97 +601,182 @@ __device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R
     }
 }
 
+// Stages the functor's rows of line t (n elements each) into pre[a][field][H]: 16-byte
+// copies where the rows allow them, else 4-byte ones.  Does not commit.
+template <typename R, class Fn>
+__device__ __forceinline__ void prefetch_rows(const Fn &fn, R *pre, int t, int n) {
+    constexpr int V4 = 16 / sizeof(R);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < Fn::NPRE; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const R *src = fn.pre_src(a, i);
+            if (!src) continue;
+            src += (size_t)t * n;
+            R *dst = pre + (a * 2 + i) * H;
+            if (n % V4 == 0 && ((uintptr_t)src & 15) == 0) {
+                for (int q = lane; q < n / V4; q += 32) cp_async16(dst + q * V4, src + q * V4);
+            } else {
+                for (int j = lane; j < n; j += 32) cp_async4(dst + j, src + j);
+            }
+        }
+}
+
 template <typename R>
 __device__ __forceinline__ cpx<R> *sel_buf(const OpView<R> &o, int sel) {  // 0 = Z, 1 = W, 2 = V
     return sel == 0 ? o.Z : (sel == 1 ? o.W : o.V);
 }
 
-// Forward joint row pass: line t of both fields (through the prologue functor) ->
-// half spectra out[r][kx][iy], t = r lpl + iy.
-template <typename R, class Pro, int NW, int G>
-__global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512w(View2<R> V, int nlines, int lpl, int n_in, int out_sel,
+// Shared memory of the persistent row passes (complex words): per team two tiles,
+// per warp a transform buffer and the staged functor rows.
+template <typename R, int NPRE>
+constexpr int row_warp_words() {
+    return N + (NPRE * 2 * H * (int)sizeof(R) + (int)sizeof(cpx<R>) - 1) / (int)sizeof(cpx<R>);
+}
+template <typename R, int NW, int NPRE>
+constexpr int row_t_words() {
+    return (NW / TEAM) * 2 * 2 * FS + NW * row_warp_words<R, NPRE>();
+}
+
+// Group q of a layer-major sequence (gpl groups per layer): layer, first line.
+__device__ __forceinline__ void group_lines(int q, int gpl, int lpl, int &r, int &iy0, int &ng) {
+    r = q / gpl;
+    iy0 = (q - r * gpl) * TEAM;
+    ng = min(TEAM, lpl - iy0);
+}
+
+// Forward joint row pass: line r lpl + iy of both fields (through the prologue
+// functor) -> half spectra out[r][kx][iy].
+template <typename R, class Pro, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, int lpl, int n_in, int out_sel,
                                                             Pro pro, const int *done) {
     using C = cpx<R>;
-    constexpr int P = G + 1;
+    static_assert(NW % TEAM == 0, "whole teams");
+    constexpr int NT = NW / TEAM;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (N + 2 * NC * P);
-    C *stage = buf + N;
+    const int team = warp / TEAM, k = warp % TEAM, tid = threadIdx.x - team * TEAM * 32;
+    C *tiles = reinterpret_cast<C *>(smem_raw) + (size_t)team * 2 * 2 * FS;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)NT * 2 * 2 * FS + (size_t)warp * row_warp_words<R, Pro::NPRE>();
+    R *pre = reinterpret_cast<R *>(buf + N);
     __shared__ double red[128];
     pro.init();
     LaneTw<R> tw;
     tw.load_fwd(V.op[0].twx);
-    const long long Wt = seg_warps((long long)gridDim.x * NW, nlines);
-    const long long w = (long long)blockIdx.x * NW + warp;
-    if (w < Wt) {
-        const int t0 = (int)seg_begin(w, nlines, Wt), t1 = (int)seg_begin(w + 1, nlines, Wt);
+    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const long long NG = (long long)nz * gpl;
+    const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
+    const long long tm = (long long)blockIdx.x * NT + team;
+    if (tm < Tt) {
+        const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         C *out0 = sel_buf(V.op[0], out_sel), *out1 = sel_buf(V.op[1], out_sel);
-        int gs = -1;
-        for (int t = t0; t < t1; ++t) {
-            const int r = t / lpl, iy = t - r * lpl, g = iy % G;
-            if (gs < 0) gs = g;
+        int r, iy0, ng;
+        group_lines(q0, gpl, lpl, r, iy0, ng);
+        if (k < ng) prefetch_rows(pro, pre, r * lpl + iy0 + k, n_in);
+        cp_async_commit();
+        for (int q = q0; q < q1; ++q) {
+            group_lines(q, gpl, lpl, r, iy0, ng);
+            C *tile = tiles + (q & 1) * 2 * FS;
+            const bool act = k < ng;  // this warp has a line in group q
             R a[8], b[8];
-            {
+            if (act) {
+                const int t = r * lpl + iy0 + k;
+                cp_async_wait<0>();
+                __syncwarp();
                 R a0[4], b0[4], a1[4], b1[4];
-                pro.template fetch_batch<4>(t, t, true, lane, 32, n_in, a0, b0);
-                pro.template fetch_batch<4>(t, t, true, lane + 128, 32, n_in, a1, b1);
+                pro.template fetch_batch<4, true>(t, t, true, lane, 32, n_in, a0, b0, pre);
+                pro.template fetch_batch<4, true>(t, t, true, lane + 128, 32, n_in, a1, b1, pre);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
-            }
-            C v[16];
-            fwd512_from_lines<R>(a, b, buf, tw, v);
-            split_to_stage<R, P>(v, stage, g);
-            if (g == G - 1 || t == t1 - 1 || iy == lpl - 1) {
                 __syncwarp();
-                const size_t off = (size_t)r * NC * H + (iy - g);
-                stage_store<R, G>(stage, out0 + off, out1 + off, gs, g);
-                __syncwarp();
-                gs = -1;
             }
+            if (q + 1 < q1) {  // the rows of this warp's line in the next group
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                if (k < ng2) prefetch_rows(pro, pre, r2 * lpl + iy2 + k, n_in);
+            }
+            cp_async_commit();
+            if (act) {
+                C v[16];
+                fwd512_from_lines<R>(a, b, buf, tw, v);
+                split_to_stage<R>(v, tile, k);
+            }
+            team_barrier(team);  // the group's tile is complete; the other tile is free again
+            const size_t off = (size_t)r * NC * H + iy0;
+            team_store<R>(tile, out0 + off, out1 + off, ng, tid);
         }
     }
     pro.flush(red);
 }
 
-// Inverse joint row pass: half spectra in[r][kx][iy] -> line t of both fields,
-// cropped to n_out, through the epilogue functor.
-template <typename R, class Epi, int NW, int G>
-__global__ void __launch_bounds__(NW * 32, 1) k_row_inv512w(View2<R> V, int nlines, int lpl, int n_out, int in_sel,
+// Inverse joint row pass: half spectra in[r][kx][iy] -> line r lpl + iy of both
+// fields, cropped to n_out, through the epilogue functor.  Copy groups in flight
+// at the top of group q: [tile of q], [rows of q's line].
+template <typename R, class Epi, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, int lpl, int n_out, int in_sel,
                                                             Epi epi, const int *done) {
     using C = cpx<R>;
-    constexpr int P = G + 1;
+    static_assert(NW % TEAM == 0, "whole teams");
+    constexpr int NT = NW / TEAM;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)warp * (N + 2 * NC * P);
-    C *stage = buf + N;
+    const int team = warp / TEAM, k = warp % TEAM, tid = threadIdx.x - team * TEAM * 32;
+    C *tiles = reinterpret_cast<C *>(smem_raw) + (size_t)team * 2 * 2 * FS;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)NT * 2 * 2 * FS + (size_t)warp * row_warp_words<R, Epi::NPRE>();
+    R *pre = reinterpret_cast<R *>(buf + N);
     __shared__ double red[128];
     epi.init();
     LaneTw<R> tw;
     tw.load_inv(V.op[0].twx);
-    const long long Wt = seg_warps((long long)gridDim.x * NW, nlines);
-    const long long w = (long long)blockIdx.x * NW + warp;
-    if (w < Wt) {
-        const int t0 = (int)seg_begin(w, nlines, Wt), t1 = (int)seg_begin(w + 1, nlines, Wt);
+    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const long long NG = (long long)nz * gpl;
+    const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
+    const long long tm = (long long)blockIdx.x * NT + team;
+    if (tm < Tt) {
+        const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         const C *in0 = sel_buf(V.op[0], in_sel), *in1 = sel_buf(V.op[1], in_sel);
-        for (int t = t0; t < t1; ++t) {
-            const int r = t / lpl, iy = t - r * lpl, g = iy % G;
-            if (t == t0 || g == 0) {  // a new run: slots g .. end of block, range or layer
-                const int ge = g + min(G - 1 - g, min(t1 - 1 - t, lpl - 1 - iy));
-                const size_t off = (size_t)r * NC * H + (iy - g);
+        int r, iy0, ng;
+        group_lines(q0, gpl, lpl, r, iy0, ng);
+        {
+            const size_t off = (size_t)r * NC * H + iy0;
+            team_load<R>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid);
+            cp_async_commit();
+            if (k < ng) prefetch_rows(epi, pre, r * lpl + iy0 + k, n_out);
+            cp_async_commit();
+        }
+        for (int q = q0; q < q1; ++q) {
+            group_lines(q, gpl, lpl, r, iy0, ng);
+            cp_async_wait<1>();  // this thread's copies of the tile of q
+            team_barrier(team);  // everyone's copies of q; the other tile is free again
+            if (q + 1 < q1) {
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                const size_t off = (size_t)r2 * NC * H + iy2;
+                team_load<R>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid);
+            }
+            cp_async_commit();
+            if (k < ng) {
+                const int t = r * lpl + iy0 + k;
+                R a[8], b[8];
+                stage_to_lines<R>(tiles + (q & 1) * 2 * FS, k, buf, tw, a, b);
+                cp_async_wait<1>();  // the rows of line t
                 __syncwarp();
-                stage_load<R, G>(stage, in0 + off, in1 + off, g, ge);
-                cp_async_wait_all();
+                R a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
+                epi.template store_batch<4, true>(t, t, true, lane, 32, n_out, a0, b0, pre);
+                epi.template store_batch<4, true>(t, t, true, lane + 128, 32, n_out, a1, b1, pre);
                 __syncwarp();
             }
-            R a[8], b[8];
-            stage_to_lines<R, P>(stage, g, buf, tw, a, b);
-            R a0[4], b0[4], a1[4], b1[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
-            epi.template store_batch<4>(t, t, true, lane, 32, n_out, a0, b0);
-            epi.template store_batch<4>(t, t, true, lane + 128, 32, n_out, a1, b1);
+            if (q + 1 < q1) {
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                if (k < ng2) prefetch_rows(epi, pre, r2 * lpl + iy2 + k, n_out);
+            }
+            cp_async_commit();
         }
     }
     epi.flush(red);
@@ -961,8 +1066,8 @@ template <typename R, int NW> inline size_t smem_row_resid() {
     const size_t t = (size_t)NC * (2 * NW + 1) > (size_t)NW * (N + 1) ? (size_t)NC * (2 * NW + 1) : (size_t)NW * (N + 1);
     return (t + NW * N + N) * sizeof(cpx<R>);
 }
-template <typename R, int NW, int G> inline size_t smem_row_w() {
-    return (size_t)NW * (N + 2 * NC * (G + 1)) * sizeof(cpx<R>);
+template <typename R, int NW, int NPRE> inline size_t smem_row_t() {
+    return (size_t)row_t_words<R, NW, NPRE>() * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_fwd() {
     return (size_t)CWARPS * (CSTAGES * (H + N) + N) * sizeof(cpx<R>);

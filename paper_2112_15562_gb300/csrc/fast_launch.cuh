@@ -23,8 +23,8 @@ inline View2<R> make_view2(const gj_op *a, const gj_op *b) {
 
 // row-pass shapes: cell lines use 8 warps x 2 transforms, data lines 4 warps x 1
 constexpr int kCellNW = 8, kCellFPW = 2, kDataNW = 4, kDataFPW = 1;
-// persistent joint row passes: warps per CTA (one CTA per SM), lines per staging run
-constexpr int kRowNW = 12, kRowG = 2;
+// persistent joint row passes: warps per CTA (one CTA per SM, teams of four)
+constexpr int kRowNW = 12;
 
 template <typename R, class Pro, int NW, int FPW>
 inline void set_row_fwd_attr() {
@@ -39,12 +39,12 @@ inline void set_row_resid_attr() {
     allow_max_smem(k_row_resid512<R, Epi, NW>);
 }
 template <typename R, class Pro>
-inline void set_row_fwd_w_attr() {
-    allow_max_smem(k_row_fwd512w<R, Pro, kRowNW, kRowG>);
+inline void set_row_fwd_t_attr() {
+    allow_max_smem(k_row_fwd512t<R, Pro, kRowNW>);
 }
 template <typename R, class Epi>
-inline void set_row_inv_w_attr() {
-    allow_max_smem(k_row_inv512w<R, Epi, kRowNW, kRowG>);
+inline void set_row_inv_t_attr() {
+    allow_max_smem(k_row_inv512t<R, Epi, kRowNW>);
 }
 template <typename R>
 inline void set_col_attr() {
@@ -75,18 +75,18 @@ inline void row_resid(const View2<R> &V, int nlines, int n_out, const Epi &epi, 
                                                                                                  done);
 }
 
-// persistent joint row passes over nlines lines (grid: one CTA per SM)
+// persistent joint row passes over nz layers of lpl lines (grid: one CTA per SM)
 template <typename R, class Pro>
-inline void row_fwd_w(const View2<R> &V, int grid, int nlines, int lpl, int n_in, int out_sel, const Pro &pro,
+inline void row_fwd_t(const View2<R> &V, int grid, int nz, int lpl, int n_in, int out_sel, const Pro &pro,
                       const int *done, cudaStream_t st) {
-    k_row_fwd512w<R, Pro, kRowNW, kRowG><<<grid, kRowNW * 32, smem_row_w<R, kRowNW, kRowG>(), st>>>(
-        V, nlines, lpl, n_in, out_sel, pro, done);
+    k_row_fwd512t<R, Pro, kRowNW><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Pro::NPRE>(), st>>>(
+        V, nz, lpl, n_in, out_sel, pro, done);
 }
 template <typename R, class Epi>
-inline void row_inv_w(const View2<R> &V, int grid, int nlines, int lpl, int n_out, int in_sel, const Epi &epi,
+inline void row_inv_t(const View2<R> &V, int grid, int nz, int lpl, int n_out, int in_sel, const Epi &epi,
                       const int *done, cudaStream_t st) {
-    k_row_inv512w<R, Epi, kRowNW, kRowG><<<grid, kRowNW * 32, smem_row_w<R, kRowNW, kRowG>(), st>>>(
-        V, nlines, lpl, n_out, in_sel, epi, done);
+    k_row_inv512t<R, Epi, kRowNW><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Epi::NPRE>(), st>>>(
+        V, nz, lpl, n_out, in_sel, epi, done);
 }
 
 template <typename R>

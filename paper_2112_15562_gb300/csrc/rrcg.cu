@@ -148,9 +148,14 @@ struct ProModel {
         a = mv[0];
         b = mv[1];
     }
+    // rows a line needs in every launch (m, p), staged ahead by the persistent row
+    // pass as pre[a][field][j]; the optional rows are read in place
+    static constexpr int NPRE = 2;
+    __device__ const R *pre_src(int a, int i) const { return a == 0 ? F.m[i] : (upd ? F.p[i] : nullptr); }
     // batched form: every load of the K elements is issued before any store
-    template <int K>
-    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+    template <int K, bool PRE = false>
+    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K],
+                                                const R *pre = nullptr) {
         const size_t c0 = (size_t)la * nx;
         const int r = la / ny;
         R mv[2][K], pv[2][K], wh[2][K], ma[2][K];
@@ -161,8 +166,8 @@ struct ProModel {
             const size_t c = c0 + j;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                mv[i][k] = ok ? F.m[i][c] : R(0);
-                pv[i][k] = (ok && upd) ? F.p[i][c] : R(0);
+                mv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.m[i][c]) : R(0);
+                pv[i][k] = (ok && upd) ? (PRE ? pre[(2 + i) * f512::H + j] : F.p[i][c]) : R(0);
                 wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c] : R(1);
                 ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c] : R(0);
             }
@@ -347,9 +352,11 @@ struct EpiGradient {
             acc[i] += li * li;
         }
     }
-    template <int K>
+    static constexpr int NPRE = 1;  // m, staged ahead by the persistent row pass
+    __device__ const R *pre_src(int, int i) const { return F.m[i]; }
+    template <int K, bool PRE = false>
     __device__ __forceinline__ void store_batch(int la, int, bool, int j0, int stride, int n, const R (&a)[K],
-                                                const R (&b)[K]) {
+                                                const R (&b)[K], const R *pre = nullptr) {
         const size_t c0 = (size_t)la * nx;
         const int r = la / ny;
         R mv[2][K], wh[2][K], ma[2][K], an[2][K];
@@ -359,7 +366,7 @@ struct EpiGradient {
             const bool ok = j < n;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                mv[i][k] = ok ? F.m[i][c0 + j] : R(0);
+                mv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.m[i][c0 + j]) : R(0);
                 wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
                 ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
                 an[i][k] = (ok && prev) ? F.mtp[i][c0 + j] : R(0);
@@ -433,8 +440,13 @@ struct ProDirection {
         a = x[0];
         b = x[1];
     }
-    template <int K>
-    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+    static constexpr int NPRE = 3;  // l, p, m, staged ahead by the persistent row pass
+    __device__ const R *pre_src(int a, int i) const {
+        return a == 0 ? F.l[i] : (a == 1 ? (first ? nullptr : F.p[i]) : F.m[i]);
+    }
+    template <int K, bool PRE = false>
+    __device__ __forceinline__ void fetch_batch(int la, int, bool, int j0, int stride, int n, R (&a)[K], R (&b)[K],
+                                                const R *pre = nullptr) {
         const size_t c0 = (size_t)la * nx;
         const int r = la / ny;
         R lv[2][K], pv[2][K], mv[2][K], wh[2][K], ma[2][K];
@@ -444,9 +456,9 @@ struct ProDirection {
             const bool ok = j < n;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                lv[i][k] = ok ? F.l[i][c0 + j] : R(0);
-                pv[i][k] = (ok && !first) ? F.p[i][c0 + j] : R(0);
-                mv[i][k] = ok ? F.m[i][c0 + j] : R(0);
+                lv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.l[i][c0 + j]) : R(0);
+                pv[i][k] = (ok && !first) ? (PRE ? pre[(2 + i) * f512::H + j] : F.p[i][c0 + j]) : R(0);
+                mv[i][k] = ok ? (PRE ? pre[(4 + i) * f512::H + j] : F.m[i][c0 + j]) : R(0);
                 wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
                 ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
             }
@@ -685,10 +697,10 @@ struct SolverLaunch {
         cudaFuncGetAttributes(&fa, k_scalars_after_residual);
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
-            set_row_fwd_w_attr<R, ProModel<R>>();
-            set_row_fwd_w_attr<R, ProDirection<R>>();
+            set_row_fwd_t_attr<R, ProModel<R>>();
+            set_row_fwd_t_attr<R, ProDirection<R>>();
             set_row_resid_attr<R, EpiResidual<R>, kDataNW>();
-            set_row_inv_w_attr<R, EpiGradient<R>>();
+            set_row_inv_t_attr<R, EpiGradient<R>>();
             set_row_inv_attr<R, EpiQNorm<R>, kDataNW, kDataFPW>();
             set_col_attr<R>();
             return;
@@ -748,7 +760,7 @@ struct SolverLaunch {
         if constexpr (std::is_same_v<R, float>) if (fast) {
             ProModel<R> pm{F, sv->S, o->nx, o->ny};
             using namespace f512;
-            row_fwd_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, pm, done, st);
+            row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
             forward_columns(st);
             // residual, Phi and the residual rows' spectra for the adjoint, in one pass
             EpiResidual<R> er{F, sv->S, o->sx};
@@ -773,9 +785,9 @@ struct SolverLaunch {
             using namespace f512;
             col_adj<R>(V2, o->col_grid, done, st);
             EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
-            row_inv_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, eg, done, st);
+            row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
             ProDirection<R> pd{F, sv->S, o->nx, o->ny};
-            row_fwd_w<R>(V2, o->col_grid, o->nz * o->ny, o->ny, o->nx, 0, pd, done, st);
+            row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
             row_inv<R, kDataNW, kDataFPW>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
