@@ -93,12 +93,19 @@ __device__ __forceinline__ void lp_factors(int p, R d, R eps2, R &wl, R &inv_wl)
         inv_wl = R(1);
     }
 }
+// One hardware reciprocal square root (relative error about 1e-7; arguments below
+// FLT_MIN flush to zero).  Its arguments here are d^2 + eps^2 and (d^2 + eps^2)^-1/2.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 // FP32: two reciprocal square roots, u = q^-1/2, q^1/4 = u^-1/2, q^-1/4 = u q^1/4
 template <>
 __device__ __forceinline__ void lp_factors<float>(int p, float d, float eps2, float &wl, float &inv_wl) {
     if (p == 1) {
-        const float u = rsqrtf(d * d + eps2);
-        inv_wl = rsqrtf(u);
+        const float u = rsqrt_approx(d * d + eps2);
+        inv_wl = rsqrt_approx(u);
         wl = u * inv_wl;
     } else {
         wl = 1.0f;
@@ -108,7 +115,7 @@ __device__ __forceinline__ void lp_factors<float>(int p, float d, float eps2, fl
 
 // Forward of m with the pending model update (RRCG:7-8 and the bounds) and the
 // Gramian sums of the updated models.
-template <typename R>
+template <typename R, bool OPT = true>
 struct ProModel {
     FieldVecs<R> F;
     SolverDev *S;
@@ -134,7 +141,7 @@ struct ProModel {
             R mi = F.m[i][c];
             if (upd) {
                 const R w = weight(F, i, pw[i], eps2, r, c, mi);
-                if (F.mtp[i]) F.mtp[i][c] = w * mi;  // W_k m_k, the next anchor
+                if (OPT && F.mtp[i]) F.mtp[i][c] = w * mi;  // W_k m_k, the next anchor
                 mi = mi - s[i] * F.p[i][c] / w;
                 mi = fmin(fmax(mi, lo[i]), hi[i]);
                 F.m[i][c] = mi;
@@ -168,8 +175,8 @@ struct ProModel {
             for (int i = 0; i < 2; ++i) {
                 mv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.m[i][c]) : R(0);
                 pv[i][k] = (ok && upd) ? (PRE ? pre[(2 + i) * f512::H + j] : F.p[i][c]) : R(0);
-                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c] : R(1);
-                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c] : R(0);
+                wh[i][k] = (ok && OPT && F.whard[i]) ? F.whard[i][c] : R(1);
+                ma[i][k] = (ok && OPT && F.mapr[i]) ? F.mapr[i][c] : R(0);
             }
         }
         R wd[2], iwd[2];
@@ -186,8 +193,8 @@ struct ProModel {
                     R wl, iwl;
                     lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
                     R inv_w = iwl * iwd[i];
-                    if (F.whard[i]) inv_w /= wh[i][k];
-                    if (F.mtp[i]) F.mtp[i][c] = wd[i] * wh[i][k] * wl * mv[i][k];  // W_k m_k, the next anchor
+                    if (OPT && F.whard[i]) inv_w /= wh[i][k];
+                    if (OPT && F.mtp[i]) F.mtp[i][c] = wd[i] * wh[i][k] * wl * mv[i][k];  // W_k m_k, the next anchor
                     R mi = mv[i][k] - s[i] * pv[i][k] * inv_w;
                     mi = fmin(fmax(mi, lo[i]), hi[i]);
                     F.m[i][c] = mi;
@@ -319,7 +326,7 @@ struct LoadPair {
 };
 
 // Gradient epilogue (RRCG:2-4): l = W^-1 A^T v + alpha (W m - W m_apr) + lambda l_G.
-template <typename R>
+template <typename R, bool OPT = true>
 struct EpiGradient {
     FieldVecs<R> F;
     SolverDev *S;
@@ -345,8 +352,8 @@ struct EpiGradient {
         const R lG[2] = {g22 * u0 - g12 * u1, g11 * u1 - g12 * u0};
         const R g[2] = {a, b};
         for (int i = 0; i < 2; ++i) {
-            const R ma = F.mapr[i] ? F.mapr[i][c] : R(0);
-            const R anchor = prev ? F.mtp[i][c] : w[i] * ma;
+            const R ma = (OPT && F.mapr[i]) ? F.mapr[i][c] : R(0);
+            const R anchor = (OPT && prev) ? F.mtp[i][c] : w[i] * ma;
             const R li = g[i] / w[i] + alpha[i] * (w[i] * mm[i] - anchor) + lam[i] * lG[i];
             F.l[i][c] = li;
             acc[i] += li * li;
@@ -367,9 +374,9 @@ struct EpiGradient {
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 mv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.m[i][c0 + j]) : R(0);
-                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
-                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
-                an[i][k] = (ok && prev) ? F.mtp[i][c0 + j] : R(0);
+                wh[i][k] = (ok && OPT && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
+                ma[i][k] = (ok && OPT && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
+                an[i][k] = (ok && OPT && prev) ? F.mtp[i][c0 + j] : R(0);
             }
         }
         R wd[2], iwd[2];
@@ -386,14 +393,14 @@ struct EpiGradient {
                 lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
                 w[i] = wd[i] * wl;
                 inv_w[i] = iwl * iwd[i];
-                if (F.whard[i]) { w[i] *= wh[i][k]; inv_w[i] /= wh[i][k]; }
+                if (OPT && F.whard[i]) { w[i] *= wh[i][k]; inv_w[i] /= wh[i][k]; }
             }
             const R u0 = gsp ? w[0] * mv[0][k] : mv[0][k], u1 = gsp ? w[1] * mv[1][k] : mv[1][k];
             const R lG[2] = {g22 * u0 - g12 * u1, g11 * u1 - g12 * u0};
             const R g[2] = {a[k], b[k]};
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const R anchor = prev ? an[i][k] : w[i] * ma[i][k];
+                const R anchor = (OPT && prev) ? an[i][k] : w[i] * ma[i][k];
                 const R li = g[i] * inv_w[i] + alpha[i] * (w[i] * mv[i][k] - anchor) + lam[i] * lG[i];
                 F.l[i][c0 + j] = li;
                 acc[i] += li * li;
@@ -404,7 +411,7 @@ struct EpiGradient {
 };
 
 // Search direction (RRCG:5) and the forward input W^-1 p.
-template <typename R>
+template <typename R, bool OPT = true>
 struct ProDirection {
     FieldVecs<R> F;
     SolverDev *S;
@@ -459,8 +466,8 @@ struct ProDirection {
                 lv[i][k] = ok ? (PRE ? pre[i * f512::H + j] : F.l[i][c0 + j]) : R(0);
                 pv[i][k] = (ok && !first) ? (PRE ? pre[(2 + i) * f512::H + j] : F.p[i][c0 + j]) : R(0);
                 mv[i][k] = ok ? (PRE ? pre[(4 + i) * f512::H + j] : F.m[i][c0 + j]) : R(0);
-                wh[i][k] = (ok && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
-                ma[i][k] = (ok && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
+                wh[i][k] = (ok && OPT && F.whard[i]) ? F.whard[i][c0 + j] : R(1);
+                ma[i][k] = (ok && OPT && F.mapr[i]) ? F.mapr[i][c0 + j] : R(0);
             }
         }
         R iwd[2];
@@ -477,7 +484,7 @@ struct ProDirection {
                 R wl, iwl;
                 lp_factors<R>(pw[i], mv[i][k] - ma[i][k], eps2, wl, iwl);
                 R inv_w = iwl * iwd[i];
-                if (F.whard[i]) inv_w /= wh[i][k];
+                if (OPT && F.whard[i]) inv_w /= wh[i][k];
                 if (ok) {
                     F.p[i][c0 + j] = pi;
                     acc[i] += pi * lv[i][k];
@@ -689,6 +696,14 @@ struct SolverLaunch {
         }
     }
 
+    // any optional row (hard weights, a-priori model, previous-model anchor) present:
+    // the functors' variants without them skip those loads and factors entirely
+    bool opt_rows() const {
+        for (int i = 0; i < 2; ++i)
+            if (F.whard[i] || F.mapr[i] || F.mtp[i]) return true;
+        return false;
+    }
+
     void set_attributes() {
         // Load every kernel of an iteration now: with lazy module loading, the first
         // launch of a kernel inside a stream capture would invalidate the capture.
@@ -697,10 +712,13 @@ struct SolverLaunch {
         cudaFuncGetAttributes(&fa, k_scalars_after_residual);
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
-            set_row_fwd_t_attr<R, ProModel<R>>();
-            set_row_fwd_t_attr<R, ProDirection<R>>();
+            set_row_fwd_t_attr<R, ProModel<R, true>>();
+            set_row_fwd_t_attr<R, ProDirection<R, true>>();
+            set_row_fwd_t_attr<R, ProModel<R, false>>();
+            set_row_fwd_t_attr<R, ProDirection<R, false>>();
             set_row_resid_attr<R, EpiResidual<R>, kDataNW>();
-            set_row_inv_t_attr<R, EpiGradient<R>>();
+            set_row_inv_t_attr<R, EpiGradient<R, true>>();
+            set_row_inv_t_attr<R, EpiGradient<R, false>>();
             set_row_inv_attr<R, EpiQNorm<R>, kDataNW, kDataFPW>();
             set_col_attr<R>();
             return;
@@ -758,9 +776,14 @@ struct SolverLaunch {
         const gj_op *o = sv->op[0];
         const int *done = &sv->S->done;
         if constexpr (std::is_same_v<R, float>) if (fast) {
-            ProModel<R> pm{F, sv->S, o->nx, o->ny};
             using namespace f512;
-            row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
+            if (opt_rows()) {
+                ProModel<R, true> pm{F, sv->S, o->nx, o->ny};
+                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
+            } else {
+                ProModel<R, false> pm{F, sv->S, o->nx, o->ny};
+                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
+            }
             forward_columns(st);
             // residual, Phi and the residual rows' spectra for the adjoint, in one pass
             EpiResidual<R> er{F, sv->S, o->sx};
@@ -784,10 +807,17 @@ struct SolverLaunch {
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
             col_adj<R>(V2, o->col_grid, done, st);
-            EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
-            row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
-            ProDirection<R> pd{F, sv->S, o->nx, o->ny};
-            row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
+            if (opt_rows()) {
+                EpiGradient<R, true> eg{F, sv->S, o->nx, o->ny};
+                row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
+                ProDirection<R, true> pd{F, sv->S, o->nx, o->ny};
+                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
+            } else {
+                EpiGradient<R, false> eg{F, sv->S, o->nx, o->ny};
+                row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
+                ProDirection<R, false> pd{F, sv->S, o->nx, o->ny};
+                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
+            }
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
             row_inv<R, kDataNW, kDataFPW>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);

@@ -24,18 +24,24 @@ def joint_case(w):
     return g, A, dob, sig, wdep
 
 
-def run_oracle(g, A, dob, sig, wdep, P, m0=None):
+def run_oracle(g, A, dob, sig, wdep, P, m0=None, m_apr=None, w_hard=None):
     m0 = [np.zeros(g.n)] * 2 if m0 is None else m0
+    w_static = [np.repeat(wdep[i], g.nx * g.ny) * (1.0 if w_hard is None else w_hard[i]) for i in range(2)]
     return rrcg_joint([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
-                      dob, sig, m0, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)], P)
+                      dob, sig, m0, w_static, P, m_apr=m_apr)
 
 
-def run_gpu(gj, w, g, dob, sig, wdep, prec, kw, m0=None, graph=None, npad=(0, 0)):
+def run_gpu(gj, w, g, dob, sig, wdep, prec, kw, m0=None, graph=None, npad=(0, 0), m_apr=None, w_hard=None):
     ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
            gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
     m = [to_dev(np.zeros(g.n) if m0 is None else m0[i], prec) for i in range(2)]
     args = ([to_dev(x, prec) for x in dob], [to_dev(x, prec) for x in sig], [to_dev(x, prec) for x in wdep], m)
     P = gj.solver_params(**kw)
+    if m_apr is not None or w_hard is not None:
+        opt = dict(m_apr=None if m_apr is None else [to_dev(x, prec) for x in m_apr],
+                   w_hard=None if w_hard is None else [to_dev(x, prec) for x in w_hard])
+        rep = gj.rrcg_joint_solve(ops, P, *args, history=True, **opt)
+        return [t.cpu().numpy().astype(np.float64) for t in m], rep
     if graph is None:
         rep = gj.rrcg_joint_solve(ops, P, *args, history=True)
     else:
@@ -159,3 +165,26 @@ def test_fast_graph_and_eager_agree(small, graph):
     for i in range(2):
         # dot products are summed with floating-point atomics: agreement to rounding
         assert rel(m2[i], m1[i]) <= 1e-5
+
+
+@pytest.mark.parametrize("anchor", ["apriori", "previous"])
+@pytest.mark.parametrize("path", ["fp64", "fp32_512"])
+def test_a_priori_model_and_hard_weights(small, path, anchor):
+    """m_apr in the Lp factor and the anchor (Eq. WL, RRCG:4) and W_hard in W (Eq. W),
+    on the generic FP64 kernels and on the 512 x 512 FP32 kernels."""
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    m_apr = [synth.smooth_blocky(g, 0.3, seed=21), synth.smooth_blocky(g, 0.03, seed=22)]
+    w_hard = [synth.uniform_model(g, 0.5, 2.0, seed=23), synth.uniform_model(g, 0.5, 2.0, seed=24)]
+    kw = dict(KW, kmax=20, anchor=anchor)
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw), m_apr=m_apr, w_hard=w_hard)
+    prec, npad, tol = ("fp64", (0, 0), 1e-8) if path == "fp64" else ("fp32", (512, 512), 1e-3)
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, prec, kw, npad=npad, m_apr=m_apr, w_hard=w_hard)
+    assert rep["iterations"] == 20
+    if prec == "fp64":
+        compare_history(rep["history"], ref.history, tol)
+    for k in (0, 1, 10, 19):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=tol), (k, i)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= tol, (i, rel(m[i], ref.m[i]))
