@@ -829,6 +829,24 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
 }
 
 // ---------------------------------------------------------------------------
+// Item t = (field NC + kx) nz + r of the column passes, set once by division and
+// then advanced by increments.
+struct ColItem {
+    int fld, kx, r;
+    __device__ __forceinline__ void set(int t, int nz) {
+        const int col = t / nz;
+        r = t - col * nz;
+        fld = col / NC;
+        kx = col - fld * NC;
+    }
+    __device__ __forceinline__ void next(int nz) {
+        if (++r == nz) {
+            r = 0;
+            if (++kx == NC) { kx = 0; ++fld; }
+        }
+    }
+};
+
 // Forward column pass: for each (field, kx), Y = sum_r St_r[kx] . FFT512(Zt_r[kx]),
 // then W[kx][jy] = IFFT512(Y)[jy] for jy < sy.  Persistent warps take balanced
 // contiguous segments of the (field, kx, r) sequence; a column split across warps
@@ -857,40 +875,43 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
     const long long w = (long long)blockIdx.x * CWARPS + warp;
     if (w >= Wt) return;
-    const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
+    const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
-    auto issue = [&](long long t) {
-        const int s = (int)((t - t0) % CSTAGES);
-        const int r = (int)(t % nz);
-        const long long col = t / nz;
-        const int fld = (int)(col / NC), kx = (int)(col % NC);
-        const OpView<R> &op = V.op[fld];
+    ColItem cu, ci;  // the item being consumed; (lane 0) the next one to issue
+    cu.set(t0, nz);
+    ci = cu;
+    int ti = t0;
+    auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
+        const int s = (ti - t0) % CSTAGES;
+        const OpView<R> &op = V.op[ci.fld];
+        const size_t off = (size_t)ci.r * NC + ci.kx;
         if (op.real_spec) {
             mbar_expect(&bars[warp][s], ZB + TB / 2);
-            bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + ((size_t)r * NC + kx) * N, TB / 2,
-                      &bars[warp][s]);
+            bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + off * N, TB / 2, &bars[warp][s]);
         } else {
             mbar_expect(&bars[warp][s], ZB + TB);
-            bulk_load(zs + s * H, op.Z + ((size_t)r * NC + kx) * H, ZB, &bars[warp][s]);
-            bulk_load(ts + s * N, op.spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+            bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
+            bulk_load(ts + s * N, op.spec + off * N, TB, &bars[warp][s]);
         }
+        ++ti;
+        ci.next(nz);
     };
     if (lane == 0)
-        for (long long t = t0; t < t1 && t < t0 + CSTAGES; ++t) issue(t);
+        while (ti < t1 && ti < t0 + CSTAGES) issue();
     C acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = czero<C>();
     bool ok = true;
-    long long t_fail = t1;
-    long long seg_start = t0;
-    for (long long t = t0; t < t1 && ok; ++t) {
-        const int s = (int)((t - t0) % CSTAGES);
+    int t_fail = t1;
+    int seg_start = t0;
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nz)) {
+        const int s = (t - t0) % CSTAGES;
         const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
         C v[16];
-        const bool real_t = V.op[(int)((t / nz) / NC)].real_spec;
+        const bool real_t = V.op[cu.fld].real_spec;
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = zs[s * H + l + 16 * j];
         fwd512<R>(v, xbuf, tw);
@@ -907,12 +928,11 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
             for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], ts[s * N + lam + 32 * k1]));
         }
         __syncwarp();
-        if (lane == 0 && t + CSTAGES < t1) issue(t + CSTAGES);
-        const int r = (int)(t % nz);
-        if (r == nz - 1 || t == t1 - 1) {
+        if (lane == 0 && ti < t1) issue();
+        if (cu.r == nz - 1 || t == t1 - 1) {
             // end of this warp's part of column `col`
-            const long long col = t / nz;
-            const int fld = (int)(col / NC), kx = (int)(col % NC);
+            const int fld = cu.fld, kx = cu.kx;
+            const long long col = (long long)fld * NC + kx;
             const OpView<R> &op = V.op[fld];
             const long long cb = col * nz, ce = cb + nz - 1;
             const bool whole = (seg_start <= cb) && (t == ce);
@@ -988,34 +1008,34 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
     const long long w = (long long)blockIdx.x * CWARPS + warp;
     if (w >= Wt) return;
-    const long long t0 = seg_begin(w, T, Wt), t1 = seg_begin(w + 1, T, Wt);
+    const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
-    auto issue = [&](long long t) {
-        const int s = (int)((t - t0) % CSTAGES);
-        const int r = (int)(t % nz);
-        const long long col = t / nz;
-        const int fld = (int)(col / NC), kx = (int)(col % NC);
-        if (V.op[fld].real_spec) {
+    ColItem cu, ci;  // the item being consumed; (lane 0) the next one to issue
+    cu.set(t0, nz);
+    ci = cu;
+    int ti = t0;
+    auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
+        const int s = (ti - t0) % CSTAGES;
+        const size_t off = (size_t)ci.r * NC + ci.kx;
+        if (V.op[ci.fld].real_spec) {
             mbar_expect(&bars[warp][s], TB / 2);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[fld].spec) + ((size_t)r * NC + kx) * N, TB / 2,
-                      &bars[warp][s]);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[ci.fld].spec) + off * N, TB / 2, &bars[warp][s]);
         } else {
             mbar_expect(&bars[warp][s], TB);
-            bulk_load(ts + s * N, V.op[fld].spec + ((size_t)r * NC + kx) * N, TB, &bars[warp][s]);
+            bulk_load(ts + s * N, V.op[ci.fld].spec + off * N, TB, &bars[warp][s]);
         }
+        ++ti;
+        ci.next(nz);
     };
     if (lane == 0)
-        for (long long t = t0; t < t1 && t < t0 + CSTAGES; ++t) issue(t);
+        while (ti < t1 && ti < t0 + CSTAGES) issue();
     C vh[16];
-    long long cur_col = -1;
     bool ok = true;
-    long long t_fail = t1;
-    for (long long t = t0; t < t1 && ok; ++t) {
-        const long long col = t / nz;
-        const int r = (int)(t % nz);
-        const int fld = (int)(col / NC), kx = (int)(col % NC);
+    int t_fail = t1;
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nz)) {
+        const int r = cu.r, fld = cu.fld, kx = cu.kx;
         const OpView<R> &op = V.op[fld];
-        if (col != cur_col) {
+        if (t == t0 || r == 0) {  // a new column
             // V^ = FFT512 of the residual column (rows >= sy are zero)
             const C *Wc = op.V + (size_t)kx * H;
 #pragma unroll
@@ -1023,9 +1043,8 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             tw.load_fwd(V.op[0].twy);
             fwd512<R>(vh, xbuf, tw);
             tw.load_inv(V.op[0].twy);
-            cur_col = col;
         }
-        const int s = (int)((t - t0) % CSTAGES);
+        const int s = (t - t0) % CSTAGES;
         const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
         if (!ok) { t_fail = t; break; }
@@ -1042,7 +1061,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], ts[s * N + lam + 32 * k1]);
         }
         __syncwarp();
-        if (lane == 0 && t + CSTAGES < t1) issue(t + CSTAGES);
+        if (lane == 0 && ti < t1) issue();
         C out[8];
         inv512<R>(v, xbuf, tw, out);
         C *Zc = op.Z + ((size_t)r * NC + kx) * H;
