@@ -1,0 +1,579 @@
+// Row passes of the 512 x 512 fast path (x direction): real lines <-> half spectra
+// in the transposed layout Zt[r][kx][iy] that the column passes of fast512.cuh
+// stream.  The warp FFT, the TMA helpers and the segmentation live there.
+#pragma once
+#include "fast512.cuh"
+
+namespace gj {
+namespace f512 {
+
+// ---------------------------------------------------------------------------
+// Row pass (x direction), real lines -> half spectra in the transposed layout.
+// A CTA of NW warps runs FPW complex transforms per warp (FFTS = NW * FPW per CTA).
+// Joint mode: transform f packs line (base + f) of field 0 (real part) and field 1
+// (imaginary part); single mode: lines (base + 2f, base + 2f + 1) of field 0.
+// lpl = lines per layer (ny for model lines, sy for data lines).
+
+__device__ __forceinline__ void pair_lines(int joint, int base, int f, int nlines, int &la, int &lb, bool &ha,
+                                           bool &hb) {
+    if (joint) { la = lb = base + f; ha = hb = la < nlines; }
+    else { la = base + 2 * f; lb = la + 1; ha = la < nlines; hb = lb < nlines; }
+}
+
+// Splits the staged spectra of FFTS transforms into the two real half spectra and
+// writes them to out[r][kx][iy] (the transposed layout), iy fastest.
+template <typename R, int FFTS>
+__device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const View2<R> &V, int joint, int base,
+                                                   int nlines, int lpl, int out_sel) {
+    using C = cpx<R>;
+    static_assert((FFTS & (FFTS - 1)) == 0, "FFTS must be a power of two");
+    // blockDim is a multiple of FFTS, so this thread always serves transform f
+    const int f = threadIdx.x % FFTS;
+    int la, lb;
+    bool ha, hb;
+    pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+    const int fb = joint ? 1 : 0;
+    const int ra = ha ? la / lpl : 0, rb = hb ? lb / lpl : 0;
+    C *oa = (out_sel == 0 ? V.op[0].Z : (out_sel == 1 ? V.op[0].W : V.op[0].V)) + (size_t)ra * NC * H + (la - ra * lpl);
+    C *ob = (out_sel == 0 ? V.op[fb].Z : (out_sel == 1 ? V.op[fb].W : V.op[fb].V)) + (size_t)rb * NC * H + (lb - rb * lpl);
+    const C *row = tile + f * (N + 1);
+    const int kstep = blockDim.x / FFTS;
+    for (int kx = threadIdx.x / FFTS; kx < NC; kx += kstep) {
+        const C zk = row[ppos(kx)];
+        const C zm = row[ppos((N - kx) & (N - 1))];
+        if (ha) oa[kx * H] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (hb) ob[kx * H] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    }
+}
+
+// Real input a + i b held as a[i], b[i] for elements lane + 32 i: redistribute
+// through the warp tile and run the forward transform.  Result in v (lane layout).
+template <typename R>
+__device__ __forceinline__ void fwd512_from_lines(const R (&a)[8], const R (&b)[8], cpx<R> *buf, const LaneTw<R> &tw,
+                                                  cpx<R> (&v)[16]) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, l = lane & 15;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = buf[l + 16 * j];
+    fwd512<R>(v, buf, tw);
+}
+
+template <typename R, class Pro, int NW, int FPW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint, int nlines, int lpl, int n_in,
+                                                           int out_sel, Pro pro, const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW * FPW;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [FFTS][N + 1]
+    C *xb = tile + FFTS * (N + 1);              // per warp 512
+    C *tws = xb + NW * N;                       // W512 table
+    __shared__ double red[128];
+    pro.init();
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load_fwd(V.op[0].twx);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
+    C *buf = xb + warp * N;
+    for (int s = 0; s < FPW; ++s) {
+        const int f = warp * FPW + s;
+        int la, lb;
+        bool ha, hb;
+        pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+        R a[8], b[8];
+        if (ha) {
+            // two batches of four keep the prologue's registers below the spill point
+            R a0[4], b0[4], a1[4], b1[4];
+            pro.template fetch_batch<4>(la, lb, hb, lane, 32, n_in, a0, b0);
+            pro.template fetch_batch<4>(la, lb, hb, lane + 128, 32, n_in, a1, b1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
+        }
+        C v[16];
+        fwd512_from_lines<R>(a, b, buf, tw, v);
+        const int lam = 2 * l + h;
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + ppos(lam + 32 * k1)] = v[k1];
+    }
+    __syncthreads();
+    write_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, out_sel);
+    pro.flush(red);
+}
+
+// Stages the half spectra of the CTA's lines: source column s < 2 FFTS holds
+// (joint) field s / FFTS, line base + s % FFTS, or (single) line base + s.
+template <typename R, int FFTS>
+__device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> &V, int joint, int base, int nlines,
+                                                   int lpl, int in_sel) {
+    using C = cpx<R>;
+    constexpr int SRC = 2 * FFTS, P = SRC + 1;
+    const int s = threadIdx.x % SRC;
+    const int fld = joint ? (s / FFTS) : 0;
+    const int line = joint ? base + (s % FFTS) : base + s;
+    const bool ok = line < nlines;
+    const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
+    const C *src = in_sel == 0 ? V.op[fld].Z : (in_sel == 1 ? V.op[fld].W : V.op[fld].V);
+    const C *in = src + (size_t)r * NC * H + iy;
+    const int kx0 = threadIdx.x / SRC, kstep = blockDim.x / SRC;
+    for (int kb = kx0; kb < NC; kb += 8 * kstep) {
+        C val[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kx = kb + u * kstep;
+            val[u] = (ok && kx < NC) ? in[(size_t)kx * H] : czero<C>();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kx = kb + u * kstep;
+            if (kx < NC) tile[kpos(kx) * P + s] = val[u];
+        }
+    }
+}
+
+// Gathers transform f (sources sa, sb: Hermitian-extended A + i B) in the lane
+// layout and runs the inverse transform; returns y[lane + 32 i] in a[i] + i b[i].
+template <typename R, int FFTS>
+__device__ __forceinline__ void inv512_to_lines(const cpx<R> *tile, int sa, int sb, cpx<R> *buf, const LaneTw<R> &tw,
+                                                R (&a)[8], R (&b)[8]) {
+    using C = cpx<R>;
+    constexpr int P = 2 * FFTS + 1;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    C v[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+        const int k = lam + 32 * k1;
+        const bool lo = k <= H;
+        const int kk = lo ? k : N - k;
+        C A = tile[kpos(kk) * P + sa], B = tile[kpos(kk) * P + sb];
+        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+        v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+    }
+    C out[8];
+    inv512<R>(v, buf, tw, out);
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const C y = buf[lane + 32 * i];
+        a[i] = y.x;
+        b[i] = y.y;
+    }
+}
+
+// Inverse row pass: half spectra in[r][kx][iy] -> real lines, cropped to n_out,
+// through the epilogue functor.
+template <typename R, class Epi, int NW, int FPW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint, int nlines, int lpl, int n_out,
+                                                           int in_sel, Epi epi, const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW * FPW;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 FFTS + 1]
+    C *xb = tile + NC * (2 * FFTS + 1);
+    C *tws = xb + NW * N;
+    __shared__ double red[128];
+    epi.init();
+    const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
+    stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load_inv(V.op[0].twx);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *buf = xb + warp * N;
+    for (int s2 = 0; s2 < FPW; ++s2) {
+        const int f = warp * FPW + s2;
+        const int sa = joint ? f : 2 * f;
+        const int sb = joint ? FFTS + f : 2 * f + 1;
+        R a[8], b[8];
+        inv512_to_lines<R, FFTS>(tile, sa, sb, buf, tw, a, b);
+        int la, lb;
+        bool ha, hb;
+        pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+        if (ha) {
+            R a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
+            epi.template store_batch<4>(la, lb, hb, lane, 32, n_out, a0, b0);
+            epi.template store_batch<4>(la, lb, hb, lane + 128, 32, n_out, a1, b1);
+        }
+    }
+    epi.flush(red);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent joint row passes (both fields in one complex transform per line).
+// A team of four warps takes a balanced contiguous range of the aligned four-line
+// groups of the layers (warp k of the team transforms line 4q + k of group q), so
+// that no launch ends in a partial wave.  The half spectra of a group sit in a
+// double-buffered team tile stage[field][slot][kq(kx)] and move to or from the
+// transposed layout out[r][kx][iy] as whole 32-byte sectors (four lines of one
+// column).  kq puts even columns first and odd ones from 136 on; with the slot
+// stride LS = 274 (2 mod 16), a half-warp's 16 consecutive columns of one line, and
+// its 4 x 4 (column, slot) pairs of a group, each fall in 16 distinct bank pairs.
+// One named barrier per group and team.  The rows the functor reads in every
+// launch (m, p, l) are staged one line ahead with asynchronous copies.
+
+constexpr int TEAM = 4;                 // warps per team = lines per group
+constexpr int LS = 274, FS = TEAM * LS;  // slot and field strides of a team tile (complex words)
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {  // at most NPEND of the newest groups still in flight
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+__device__ __forceinline__ void team_barrier(int team) {  // barrier 0 stays with __syncthreads
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + team), "r"(TEAM * 32) : "memory");
+}
+
+__device__ __forceinline__ int kq(int kx) { return (kx & 1) ? 136 + (kx >> 1) : (kx >> 1); }
+
+// Z = FFT(a + i b) in the lane layout (v[k1] = Z[lambda + 32 k1]) -> the half
+// spectra A = (Z[kx] + conj Z[N - kx]) / 2 and B = (Z[kx] - conj Z[N - kx]) / 2i,
+// kx = 0..256, into slot g of a team tile.  For lambda != 0, Z[N - kx] sits in
+// lane (h, 16 - l - h) at k1' = 15 - k1; lane 0 (lambda = 0) holds it at 16 - k1.
+template <typename R>
+__device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *stage, int g) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int partner = h ? 31 - l : ((16 - l) & 15);
+    C *sa = stage + g * LS, *sb = sa + FS;
+    const int q0 = h * 136 + l;  // kq(lambda + 32 k1) = q0 + 16 k1
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        C zm;
+        zm.x = __shfl_sync(0xffffffffu, v[15 - k1].x, partner);
+        zm.y = __shfl_sync(0xffffffffu, v[15 - k1].y, partner);
+        if (lane == 0) zm = v[(16 - k1) & 15];
+        const C zk = v[k1];
+        sa[q0 + 16 * k1] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        sb[q0 + 16 * k1] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+    }
+    if (lane == 0) {  // kx = 256 is its own partner
+        sa[kq(H)] = mk<C>(v[8].x, R(0));
+        sb[kq(H)] = mk<C>(v[8].y, R(0));
+    }
+}
+
+// Slot g < ng of a team tile -> oa[kx * H + g], ob[kx * H + g]; the team's 128
+// threads each take (g, kx) = (tid % 4, tid / 4 + 32 i).
+template <typename R>
+__device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid) {
+    const int g = tid % TEAM;
+    if (g >= ng) return;
+    const cpx<R> *sa = stage + g * LS, *sb = sa + FS;
+    for (int kx = tid / TEAM; kx < NC; kx += 32) {
+        oa[(size_t)kx * H + g] = sa[kq(kx)];
+        ob[(size_t)kx * H + g] = sb[kq(kx)];
+    }
+}
+
+// ia[kx * H + g], ib[kx * H + g] -> slot g < ng of a team tile (asynchronous copies).
+template <typename R>
+__device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid) {
+    const int g = tid % TEAM;
+    if (g >= ng) return;
+    cpx<R> *sa = stage + g * LS, *sb = sa + FS;
+    for (int kx = tid / TEAM; kx < NC; kx += 32) {
+        cp_async8(sa + kq(kx), ia + (size_t)kx * H + g);
+        cp_async8(sb + kq(kx), ib + (size_t)kx * H + g);
+    }
+}
+
+// Slot g of a team tile (A + i B, Hermitian-extended) -> inverse transform ->
+// y[lane + 32 i] in a[i] + i b[i].
+template <typename R>
+__device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const LaneTw<R> &tw,
+                                               R (&a)[8], R (&b)[8]) {
+    using C = cpx<R>;
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int lam = 2 * l + h;
+    const C *sa = stage + g * LS, *sb = sa + FS;
+    C v[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+        const int k = lam + 32 * k1;
+        const bool lo = k <= H;
+        const int kk = lo ? k : N - k;
+        C A = sa[kq(kk)], B = sb[kq(kk)];
+        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+        v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+    }
+    C out[8];
+    inv512<R>(v, buf, tw, out);
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) buf[l + 16 * (8 * h + jj)] = out[jj];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const C y = buf[lane + 32 * i];
+        a[i] = y.x;
+        b[i] = y.y;
+    }
+}
+
+// Stages the functor's rows of line t (n elements each) into pre[a][field][H]: 16-byte
+// copies where the rows allow them, else 4-byte ones.  Does not commit.
+template <typename R, class Fn>
+__device__ __forceinline__ void prefetch_rows(const Fn &fn, R *pre, int t, int n) {
+    constexpr int V4 = 16 / sizeof(R);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < Fn::NPRE; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const R *src = fn.pre_src(a, i);
+            if (!src) continue;
+            src += (size_t)t * n;
+            R *dst = pre + (a * 2 + i) * H;
+            if (n % V4 == 0 && ((uintptr_t)src & 15) == 0) {
+                for (int q = lane; q < n / V4; q += 32) cp_async16(dst + q * V4, src + q * V4);
+            } else {
+                for (int j = lane; j < n; j += 32) cp_async4(dst + j, src + j);
+            }
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> *sel_buf(const OpView<R> &o, int sel) {  // 0 = Z, 1 = W, 2 = V
+    return sel == 0 ? o.Z : (sel == 1 ? o.W : o.V);
+}
+
+// Shared memory of the persistent row passes (complex words): per team two tiles,
+// per warp a transform buffer and the staged functor rows.
+template <typename R, int NPRE>
+constexpr int row_warp_words() {
+    return N + (NPRE * 2 * H * (int)sizeof(R) + (int)sizeof(cpx<R>) - 1) / (int)sizeof(cpx<R>);
+}
+template <typename R, int NW, int NPRE>
+constexpr int row_t_words() {
+    return (NW / TEAM) * 2 * 2 * FS + NW * row_warp_words<R, NPRE>();
+}
+
+// Group q of a layer-major sequence (gpl groups per layer): layer, first line.
+__device__ __forceinline__ void group_lines(int q, int gpl, int lpl, int &r, int &iy0, int &ng) {
+    r = q / gpl;
+    iy0 = (q - r * gpl) * TEAM;
+    ng = min(TEAM, lpl - iy0);
+}
+
+// Forward joint row pass: line r lpl + iy of both fields (through the prologue
+// functor) -> half spectra out[r][kx][iy].
+template <typename R, class Pro, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, int lpl, int n_in, int out_sel,
+                                                            Pro pro, const int *done) {
+    using C = cpx<R>;
+    static_assert(NW % TEAM == 0, "whole teams");
+    constexpr int NT = NW / TEAM;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = warp / TEAM, k = warp % TEAM, tid = threadIdx.x - team * TEAM * 32;
+    C *tiles = reinterpret_cast<C *>(smem_raw) + (size_t)team * 2 * 2 * FS;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)NT * 2 * 2 * FS + (size_t)warp * row_warp_words<R, Pro::NPRE>();
+    R *pre = reinterpret_cast<R *>(buf + N);
+    __shared__ double red[128];
+    pro.init();
+    LaneTw<R> tw;
+    tw.load_fwd(V.op[0].twx);
+    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const long long NG = (long long)nz * gpl;
+    const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
+    const long long tm = (long long)blockIdx.x * NT + team;
+    if (tm < Tt) {
+        const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
+        C *out0 = sel_buf(V.op[0], out_sel), *out1 = sel_buf(V.op[1], out_sel);
+        int r, iy0, ng;
+        group_lines(q0, gpl, lpl, r, iy0, ng);
+        if (k < ng) prefetch_rows(pro, pre, r * lpl + iy0 + k, n_in);
+        cp_async_commit();
+        for (int q = q0; q < q1; ++q) {
+            group_lines(q, gpl, lpl, r, iy0, ng);
+            C *tile = tiles + (q & 1) * 2 * FS;
+            const bool act = k < ng;  // this warp has a line in group q
+            R a[8], b[8];
+            if (act) {
+                const int t = r * lpl + iy0 + k;
+                cp_async_wait<0>();
+                __syncwarp();
+                R a0[4], b0[4], a1[4], b1[4];
+                pro.template fetch_batch<4, true>(t, t, true, lane, 32, n_in, a0, b0, pre);
+                pro.template fetch_batch<4, true>(t, t, true, lane + 128, 32, n_in, a1, b1, pre);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
+                __syncwarp();
+            }
+            if (q + 1 < q1) {  // the rows of this warp's line in the next group
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                if (k < ng2) prefetch_rows(pro, pre, r2 * lpl + iy2 + k, n_in);
+            }
+            cp_async_commit();
+            if (act) {
+                C v[16];
+                fwd512_from_lines<R>(a, b, buf, tw, v);
+                split_to_stage<R>(v, tile, k);
+            }
+            team_barrier(team);  // the group's tile is complete; the other tile is free again
+            const size_t off = (size_t)r * NC * H + iy0;
+            team_store<R>(tile, out0 + off, out1 + off, ng, tid);
+        }
+    }
+    pro.flush(red);
+}
+
+// Inverse joint row pass: half spectra in[r][kx][iy] -> line r lpl + iy of both
+// fields, cropped to n_out, through the epilogue functor.  Copy groups in flight
+// at the top of group q: [tile of q], [rows of q's line].
+template <typename R, class Epi, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, int lpl, int n_out, int in_sel,
+                                                            Epi epi, const int *done) {
+    using C = cpx<R>;
+    static_assert(NW % TEAM == 0, "whole teams");
+    constexpr int NT = NW / TEAM;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = warp / TEAM, k = warp % TEAM, tid = threadIdx.x - team * TEAM * 32;
+    C *tiles = reinterpret_cast<C *>(smem_raw) + (size_t)team * 2 * 2 * FS;
+    C *buf = reinterpret_cast<C *>(smem_raw) + (size_t)NT * 2 * 2 * FS + (size_t)warp * row_warp_words<R, Epi::NPRE>();
+    R *pre = reinterpret_cast<R *>(buf + N);
+    __shared__ double red[128];
+    epi.init();
+    LaneTw<R> tw;
+    tw.load_inv(V.op[0].twx);
+    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const long long NG = (long long)nz * gpl;
+    const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
+    const long long tm = (long long)blockIdx.x * NT + team;
+    if (tm < Tt) {
+        const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
+        const C *in0 = sel_buf(V.op[0], in_sel), *in1 = sel_buf(V.op[1], in_sel);
+        int r, iy0, ng;
+        group_lines(q0, gpl, lpl, r, iy0, ng);
+        {
+            const size_t off = (size_t)r * NC * H + iy0;
+            team_load<R>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid);
+            cp_async_commit();
+            if (k < ng) prefetch_rows(epi, pre, r * lpl + iy0 + k, n_out);
+            cp_async_commit();
+        }
+        for (int q = q0; q < q1; ++q) {
+            group_lines(q, gpl, lpl, r, iy0, ng);
+            cp_async_wait<1>();  // this thread's copies of the tile of q
+            team_barrier(team);  // everyone's copies of q; the other tile is free again
+            if (q + 1 < q1) {
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                const size_t off = (size_t)r2 * NC * H + iy2;
+                team_load<R>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid);
+            }
+            cp_async_commit();
+            if (k < ng) {
+                const int t = r * lpl + iy0 + k;
+                R a[8], b[8];
+                stage_to_lines<R>(tiles + (q & 1) * 2 * FS, k, buf, tw, a, b);
+                cp_async_wait<1>();  // the rows of line t
+                __syncwarp();
+                R a0[4], b0[4], a1[4], b1[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
+                epi.template store_batch<4, true>(t, t, true, lane, 32, n_out, a0, b0, pre);
+                epi.template store_batch<4, true>(t, t, true, lane + 128, 32, n_out, a1, b1, pre);
+                __syncwarp();
+            }
+            if (q + 1 < q1) {
+                int r2, iy2, ng2;
+                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                if (k < ng2) prefetch_rows(epi, pre, r2 * lpl + iy2 + k, n_out);
+            }
+            cp_async_commit();
+        }
+    }
+    epi.flush(red);
+}
+
+// Fused data-line pass of the solver: for station row jy of both fields, inverse
+// row transform of W (the cropped forward product), the residual epilogue
+// (r~ = W_d (A m - d), v = W_d r~, Phi partials), then the forward row transform
+// of v written to V[kx][jy] for the adjoint's column pass.
+template <typename R, class Epi, int NW>
+__global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nlines, int n_out, Epi epi,
+                                                             const int *done) {
+    using C = cpx<R>;
+    constexpr int FFTS = NW;  // one joint transform per warp
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);  // [NC][2 NW + 1], later [NW][N + 1]
+    C *xb = tile + (NC * (2 * FFTS + 1) > FFTS * (N + 1) ? NC * (2 * FFTS + 1) : FFTS * (N + 1));
+    C *tws = xb + NW * N;
+    __shared__ double red[128];
+    epi.init();
+    const int base = blockIdx.x * FFTS;
+    stage_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 1);
+    __syncthreads();
+    LaneTw<R> tw;
+    tw.load_inv(V.op[0].twx);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    C *buf = xb + warp * N;
+    const int f = warp;
+    R a[8], b[8];
+    inv512_to_lines<R, FFTS>(tile, f, FFTS + f, buf, tw, a, b);
+    tw.load_fwd(V.op[0].twx);
+    const int line = base + f;
+    const bool ok = line < nlines;
+    if (ok) {
+        epi.template resid_batch<8>(line, lane, 32, n_out, a, b);  // a, b <- v of both fields
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);
+    }
+    C v[16];
+    fwd512_from_lines<R>(a, b, buf, tw, v);
+    __syncthreads();  // every warp is done reading the staged input
+    const int lam = 2 * l + h;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + ppos(lam + 32 * k1)] = v[k1];
+    __syncthreads();
+    write_half_spectra<R, FFTS>(tile, V, 1, base, nlines, nlines, 2);
+    epi.flush(red);
+}
+
+// shared-memory bytes of each row kernel
+template <typename R, int NW, int FPW> inline size_t smem_row_fwd() {
+    return (size_t)(NW * FPW * (N + 1) + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW, int FPW> inline size_t smem_row_inv() {
+    return (size_t)(NC * (2 * NW * FPW + 1) + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW> inline size_t smem_row_resid() {
+    const size_t t = (size_t)NC * (2 * NW + 1) > (size_t)NW * (N + 1) ? (size_t)NC * (2 * NW + 1) : (size_t)NW * (N + 1);
+    return (t + NW * N + N) * sizeof(cpx<R>);
+}
+template <typename R, int NW, int NPRE> inline size_t smem_row_t() {
+    return (size_t)row_t_words<R, NW, NPRE>() * sizeof(cpx<R>);
+}
+
+}  // namespace f512
+}  // namespace gj

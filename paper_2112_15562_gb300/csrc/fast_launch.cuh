@@ -1,6 +1,6 @@
 // Host-side launch helpers of the 512 x 512 fast path.
 #pragma once
-#include "fast512.cuh"
+#include "fast512_rows.cuh"
 #include "view.cuh"
 
 namespace gj {
