@@ -298,6 +298,7 @@ struct StorePlain {
     R *y0;
     R *y1;
     int pitch;
+    __device__ __forceinline__ void prefetch(int, int, bool, int, int) const {}
     __device__ void init() {}
     __device__ __forceinline__ void store(int la, int lb, bool hb, int j, R a, R b) const {
         y0[(size_t)la * pitch + j] = a;

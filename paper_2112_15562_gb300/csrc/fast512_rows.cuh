@@ -7,6 +7,22 @@
 namespace gj {
 namespace f512 {
 
+// asynchronous global -> shared copies (cp.async), completed per thread by groups
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {  // at most NPEND of the newest groups still in flight
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Row pass (x direction), real lines -> half spectra in the transposed layout.
 // A CTA of NW warps runs FPW complex transforms per warp (FFTS = NW * FPW per CTA).
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
 
 // Stages the half spectra of the CTA's lines: source column s < 2 FFTS holds
 // (joint) field s / FFTS, line base + s % FFTS, or (single) line base + s.
+// The caller synchronises the block before reading the tile.
 template <typename R, int FFTS>
 __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> &V, int joint, int base, int nlines,
                                                    int lpl, int in_sel) {
@@ -123,19 +140,15 @@ __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> 
     const C *src = in_sel == 0 ? V.op[fld].Z : (in_sel == 1 ? V.op[fld].W : V.op[fld].V);
     const C *in = src + (size_t)r * NC * H + iy;
     const int kx0 = threadIdx.x / SRC, kstep = blockDim.x / SRC;
-    for (int kb = kx0; kb < NC; kb += 8 * kstep) {
-        C val[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int kx = kb + u * kstep;
-            val[u] = (ok && kx < NC) ? in[(size_t)kx * H] : czero<C>();
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int kx = kb + u * kstep;
-            if (kx < NC) tile[kpos(kx) * P + s] = val[u];
-        }
+    // every copy in flight at once; sources past the last line read as zero (their
+    // lane may pair with a valid line in the same complex transform)
+    for (int kx = kx0; kx < NC; kx += kstep) {
+        C *dst = tile + kpos(kx) * P + s;
+        if (ok) cp_async8(dst, in + (size_t)kx * H);
+        else *dst = czero<C>();
     }
+    cp_async_commit();
+    cp_async_wait<0>();  // the caller's barrier publishes the tile
 }
 
 // Gathers transform f (sources sa, sb: Hermitian-extended A + i B) in the lane
@@ -196,11 +209,12 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
         const int f = warp * FPW + s2;
         const int sa = joint ? f : 2 * f;
         const int sb = joint ? FFTS + f : 2 * f + 1;
-        R a[8], b[8];
-        inv512_to_lines<R, FFTS>(tile, sa, sb, buf, tw, a, b);
         int la, lb;
         bool ha, hb;
         pair_lines(joint, base, f, nlines, la, lb, ha, hb);
+        if (ha) epi.prefetch(la, lb, hb, lane, n_out);  // the epilogue's rows load during the transform
+        R a[8], b[8];
+        inv512_to_lines<R, FFTS>(tile, sa, sb, buf, tw, a, b);
         if (ha) {
             R a0[4], b0[4], a1[4], b1[4];
 #pragma unroll
@@ -228,20 +242,6 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
 constexpr int TEAM = 4;                 // warps per team = lines per group
 constexpr int LS = 274, FS = TEAM * LS;  // slot and field strides of a team tile (complex words)
 
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() {  // at most NPEND of the newest groups still in flight
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
 __device__ __forceinline__ void team_barrier(int team) {  // barrier 0 stays with __syncthreads
     asm volatile("bar.sync %0, %1;\n" ::"r"(1 + team), "r"(TEAM * 32) : "memory");
 }
@@ -281,10 +281,13 @@ template <typename R>
 __device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid) {
     const int g = tid % TEAM;
     if (g >= ng) return;
-    const cpx<R> *sa = stage + g * LS, *sb = sa + FS;
-    for (int kx = tid / TEAM; kx < NC; kx += 32) {
-        oa[(size_t)kx * H + g] = sa[kq(kx)];
-        ob[(size_t)kx * H + g] = sb[kq(kx)];
+    // kx += 32 keeps its parity, so kq(kx) advances by 16
+    int kx = tid / TEAM;
+    const cpx<R> *sa = stage + g * LS + kq(kx);
+    size_t o = (size_t)kx * H + g;
+    for (; kx < NC; kx += 32, sa += 16, o += 32 * H) {
+        oa[o] = sa[0];
+        ob[o] = sa[FS];
     }
 }
 
@@ -293,10 +296,12 @@ template <typename R>
 __device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid) {
     const int g = tid % TEAM;
     if (g >= ng) return;
-    cpx<R> *sa = stage + g * LS, *sb = sa + FS;
-    for (int kx = tid / TEAM; kx < NC; kx += 32) {
-        cp_async8(sa + kq(kx), ia + (size_t)kx * H + g);
-        cp_async8(sb + kq(kx), ib + (size_t)kx * H + g);
+    int kx = tid / TEAM;  // as in team_store
+    cpx<R> *sa = stage + g * LS + kq(kx);
+    size_t o = (size_t)kx * H + g;
+    for (; kx < NC; kx += 32, sa += 16, o += 32 * H) {
+        cp_async8(sa, ia + o);
+        cp_async8(sa + FS, ib + o);
     }
 }
 
@@ -538,13 +543,15 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_resid512(View2<R> V, int nli
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     C *buf = xb + warp * N;
     const int f = warp;
+    const int line = base + f;
+    const bool ok = line < nlines;
+    R wv[2][8], dv[2][8];  // W_d and d of the line, loaded during the transform
+    if (ok) epi.template resid_load<8>(line, lane, 32, n_out, wv, dv);
     R a[8], b[8];
     inv512_to_lines<R, FFTS>(tile, f, FFTS + f, buf, tw, a, b);
     tw.load_fwd(V.op[0].twx);
-    const int line = base + f;
-    const bool ok = line < nlines;
     if (ok) {
-        epi.template resid_batch<8>(line, lane, 32, n_out, a, b);  // a, b <- v of both fields
+        epi.template resid_apply<8>(lane, 32, n_out, wv, dv, a, b);  // a, b <- v of both fields
     } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) a[i] = b[i] = R(0);

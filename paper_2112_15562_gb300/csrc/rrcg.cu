@@ -242,11 +242,11 @@ struct EpiResidual {
             F.v[i][t] = w * rt;
         }
     }
-    // fused form: y in a, b on entry; v = W_d r~ of both fields in a, b on return
+    // fused form, in two steps so that the loads can be issued before the transform:
+    // resid_load fetches W_d and d; resid_apply takes y in a, b and returns v = W_d r~
     template <int K>
-    __device__ __forceinline__ void resid_batch(int la, int j0, int stride, int n, R (&a)[K], R (&b)[K]) {
+    __device__ __forceinline__ void resid_load(int la, int j0, int stride, int n, R (&w)[2][K], R (&d)[2][K]) const {
         const size_t t0 = (size_t)la * sx;
-        R w[2][K], d[2][K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -257,6 +257,10 @@ struct EpiResidual {
                 d[i][k] = ok ? F.dobs[i][t0 + j] : R(0);
             }
         }
+    }
+    template <int K>
+    __device__ __forceinline__ void resid_apply(int j0, int stride, int n, const R (&w)[2][K], const R (&d)[2][K],
+                                                R (&a)[K], R (&b)[K]) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -517,15 +521,27 @@ struct EpiQNorm {
         acc[0] += q0 * q0;
         acc[1] += q1 * q1;
     }
-    template <int K>
-    __device__ __forceinline__ void store_batch(int la, int, bool, int j0, int stride, int n, const R (&a)[K],
-                                                const R (&b)[K]) {
+    // batched form (the 512 kernels): prefetch loads W_d of line la, elements
+    // lane + 32 k, before the transform; store_batch(j0 = lane or lane + 128) uses them
+    R wq[2][8];
+    __device__ __forceinline__ void prefetch(int la, int, bool, int lane, int n) {
         const size_t t0 = (size_t)la * sx;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = lane + 32 * k;
+            wq[0][k] = j < n ? F.wd[0][t0 + j] : R(0);
+            wq[1][k] = j < n ? F.wd[1][t0 + j] : R(0);
+        }
+    }
+    template <int K>
+    __device__ __forceinline__ void store_batch(int, int, bool, int j0, int stride, int n, const R (&a)[K],
+                                                const R (&b)[K]) {
+        const int o = (j0 - (int)(threadIdx.x & 31)) / 32;  // 0 or 4
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
             if (j >= n) continue;
-            const R q0 = F.wd[0][t0 + j] * a[k], q1 = F.wd[1][t0 + j] * b[k];
+            const R q0 = wq[0][o + k] * a[k], q1 = wq[1][o + k] * b[k];
             acc[0] += q0 * q0;
             acc[1] += q1 * q1;
         }
