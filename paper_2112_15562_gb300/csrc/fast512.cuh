@@ -139,6 +139,36 @@ struct LaneTw {
         const cpx<R> w = (k & 3) == 0 ? hi[k >> 2] : cmul(lo[k & 3], hi[k >> 2]);
         return cmul(a, w);
     }
+    // combine twiddle of the inverse, W512^(l + 16 j) (j known at compile time)
+    __device__ __forceinline__ cpx<R> cmb(int j) const { return cmul(pre, w32c<R>(j)); }
+};
+
+// The same twiddles read from a per-CTA shared-memory table (no per-lane products,
+// no twiddle registers), rows of 32 lanes (h, l):
+//   [k < 16]       forward W512^(h l + 2 l k)  (fwd_tw)
+//   [16 + k]       inverse W256^(l k) = W512^(2 l k)  (mul256)
+//   [32 + jj < 40] combine W512^(l + 16 (8 h + jj))  (cmb)
+// The entries are the operator's W512 table itself, so they carry no product rounding.
+template <typename R>
+struct TabTw {
+    static constexpr int WORDS = 40 * 32;
+    const cpx<R> *t;  // shared
+    int lane;
+    // every thread of the CTA, followed by a barrier before first use
+    __device__ static void build(cpx<R> *t, const cpx<R> *__restrict__ tw512) {
+        for (int i = threadIdx.x; i < WORDS; i += blockDim.x) {
+            const int row = i >> 5, ln = i & 31, h = ln >> 4, l = ln & 15;
+            const int e = row < 16 ? h * l + 2 * l * row : (row < 32 ? 2 * l * (row - 16) : l + 16 * (8 * h + row - 32));
+            t[i] = __ldg(tw512 + (e & 511));
+        }
+    }
+    __device__ void bind(const cpx<R> *tab) { t = tab; lane = threadIdx.x & 31; }
+    template <bool INV> __device__ __forceinline__ cpx<R> mul256(cpx<R> a, int k) const {
+        const cpx<R> w = t[(16 + k) * 32 + lane];
+        return INV ? cmulc(a, w) : cmul(a, w);
+    }
+    __device__ __forceinline__ cpx<R> fwd_tw(cpx<R> a, int k) const { return cmul(a, t[k * 32 + lane]); }
+    __device__ __forceinline__ cpx<R> cmb(int j) const { return t[(32 + (j & 7)) * 32 + lane]; }
 };
 
 // Parity-split position of spectrum index k (0 <= k < 512) in a staging row, so
@@ -152,9 +182,9 @@ __device__ __forceinline__ int swz(int row, int col) { return row * 16 + (col ^ 
 
 // Forward pruned 512-point transform.  In: v[j] = x[l + 16 j] (both halves).
 // Out: lane (h, k2) v[k1] = X[lambda + 32 k1].  buf: this warp's 512-entry tile.
-// tw must hold the forward form (load_fwd).
-template <typename R>
-__device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const LaneTw<R> &tw) {
+// tw: LaneTw in the forward form (load_fwd), or TabTw.
+template <typename R, class TW>
+__device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const TW &tw) {
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     cpx<R> *t = buf + h * 256;
     if (h) {
@@ -176,8 +206,8 @@ __device__ __forceinline__ void fwd512(cpx<R> (&v)[16], cpx<R> *buf, const LaneT
 // Inverse (tw in the inverse form, load_inv): in lane (h, k2) v[k1] = Y[lambda + 32 k1].  Out (unnormalised): every
 // lane of both halves holds y[n] for n = l + 16 j with j in [8h, 8h + 8):
 // out[jj] = y[l + 16 (8h + jj)], jj < 8.
-template <typename R>
-__device__ __forceinline__ void inv512(cpx<R> (&v)[16], cpx<R> *buf, const LaneTw<R> &tw, cpx<R> (&out)[8]) {
+template <typename R, class TW>
+__device__ __forceinline__ void inv512(cpx<R> (&v)[16], cpx<R> *buf, const TW &tw, cpx<R> (&out)[8]) {
     const int lane = threadIdx.x & 31, h = lane >> 4, k2 = lane & 15;
     cpx<R> *t = buf + h * 256;
     dft16<R, true>(v);  // over k1 -> index l
@@ -200,7 +230,7 @@ __device__ __forceinline__ void inv512(cpx<R> (&v)[16], cpx<R> *buf, const LaneT
         if (mine) {
             const cpx<R> z0 = h ? o : v[j];
             const cpx<R> z1 = h ? v[j] : o;
-            const cpx<R> w = cmul(tw.pre, w32c<R>(j));  // W512^(l + 16 j)
+            const cpx<R> w = tw.cmb(j);  // W512^(l + 16 j)
             out[j & 7] = cadd(z0, cmulc(z1, w));
         }
     }
@@ -309,13 +339,15 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     C *zs = reinterpret_cast<C *>(wbase);                          // CSTAGES x 256
     C *ts = reinterpret_cast<C *>(wbase + CSTAGES * ZB);            // CSTAGES x 512
     C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * (ZB + TB));   // 512
+    C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * (ZB + TB) + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
     if (lane == 0)
         for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
+    TabTw<R>::build(tab, V.op[0].twy);
     __syncthreads();
-    LaneTw<R> tw;
-    tw.load_fwd(V.op[0].twy);
+    TabTw<R> tw;
+    tw.bind(tab);
     const int nz = V.op[0].nz, sy = V.op[0].sy;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
@@ -372,7 +404,13 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
             }
         } else {
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = cadd(acc[k1], cmul(v[k1], ts[s * N + lam + 32 * k1]));
+            for (int k1 = 0; k1 < 16; ++k1) {  // acc += v * t, four fused multiply-adds
+                const C t = ts[s * N + lam + 32 * k1];
+                acc[k1].x = fma(v[k1].x, t.x, acc[k1].x);
+                acc[k1].x = fma(-v[k1].y, t.y, acc[k1].x);
+                acc[k1].y = fma(v[k1].x, t.y, acc[k1].y);
+                acc[k1].y = fma(v[k1].y, t.x, acc[k1].y);
+            }
         }
         __syncwarp();
         if (lane == 0 && ti < t1) issue();
@@ -412,9 +450,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
                 }
             }
             C out[8];
-            tw.load_inv(V.op[0].twy);
             inv512<R>(acc, xbuf, tw, out);
-            tw.load_fwd(V.op[0].twy);
             C *Wc = op.W + (size_t)kx * H;
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
@@ -442,13 +478,15 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     unsigned char *wbase = smem_raw + (size_t)warp * (CSTAGES * TB + N * sizeof(C));
     C *ts = reinterpret_cast<C *>(wbase);
     C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * TB);
+    C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * TB + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
     if (lane == 0)
         for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
     mbar_fence_init();
+    TabTw<R>::build(tab, V.op[0].twy);
     __syncthreads();
-    LaneTw<R> tw;
-    tw.load_inv(V.op[0].twy);
+    TabTw<R> tw;
+    tw.bind(tab);
     const int nz = V.op[0].nz, ny = V.op[0].ny;
     const long long T = (long long)V.nfield * NC * nz;
     // at most T warps take part, so that every segment holds at least one item
@@ -487,9 +525,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             const C *Wc = op.V + (size_t)kx * H;
 #pragma unroll
             for (int j = 0; j < 16; ++j) vh[j] = Wc[l + 16 * j];
-            tw.load_fwd(V.op[0].twy);
             fwd512<R>(vh, xbuf, tw);
-            tw.load_inv(V.op[0].twy);
         }
         const int s = (t - t0) % CSTAGES;
         const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
@@ -523,10 +559,10 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
 
 // shared-memory bytes of each kernel
 template <typename R> inline size_t smem_col_fwd() {
-    return (size_t)CWARPS * (CSTAGES * (H + N) + N) * sizeof(cpx<R>);
+    return ((size_t)CWARPS * (CSTAGES * (H + N) + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_adj() {
-    return (size_t)CWARPS * (CSTAGES * N + N) * sizeof(cpx<R>);
+    return ((size_t)CWARPS * (CSTAGES * N + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
 }
 
 }  // namespace f512

@@ -64,8 +64,8 @@ __device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const Vie
 
 // Real input a + i b held as a[i], b[i] for elements lane + 32 i: redistribute
 // through the warp tile and run the forward transform.  Result in v (lane layout).
-template <typename R>
-__device__ __forceinline__ void fwd512_from_lines(const R (&a)[8], const R (&b)[8], cpx<R> *buf, const LaneTw<R> &tw,
+template <typename R, class TW>
+__device__ __forceinline__ void fwd512_from_lines(const R (&a)[8], const R (&b)[8], cpx<R> *buf, const TW &tw,
                                                   cpx<R> (&v)[16]) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, l = lane & 15;
@@ -153,8 +153,8 @@ __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> 
 
 // Gathers transform f (sources sa, sb: Hermitian-extended A + i B) in the lane
 // layout and runs the inverse transform; returns y[lane + 32 i] in a[i] + i b[i].
-template <typename R, int FFTS>
-__device__ __forceinline__ void inv512_to_lines(const cpx<R> *tile, int sa, int sb, cpx<R> *buf, const LaneTw<R> &tw,
+template <typename R, int FFTS, class TW>
+__device__ __forceinline__ void inv512_to_lines(const cpx<R> *tile, int sa, int sb, cpx<R> *buf, const TW &tw,
                                                 R (&a)[8], R (&b)[8]) {
     using C = cpx<R>;
     constexpr int P = 2 * FFTS + 1;
@@ -307,8 +307,8 @@ __device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const
 
 // Slot g of a team tile (A + i B, Hermitian-extended) -> inverse transform ->
 // y[lane + 32 i] in a[i] + i b[i].
-template <typename R>
-__device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const LaneTw<R> &tw,
+template <typename R, class TW>
+__device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const TW &tw,
                                                R (&a)[8], R (&b)[8]) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
