@@ -153,6 +153,16 @@ def small_joint(seed: int = 1) -> Workload:
     return Workload("joint-16x16x8", g, Mag(50000.0, 60.0, 10.0), (m1, m2), (e[0], e[1]))
 
 
+def ragged_joint(seed: int = 6) -> Workload:
+    """15x13 stations, 15x13x6 cubes of 50 m (13 rows per layer, not a multiple of
+    four); smooth plus blocky models."""
+    g = uniform_grid(15, 13, 15, 13, 6, 50.0)
+    m1 = smooth_blocky(g, 0.5, seed, n_boxes=3, sigma=2.0)
+    m2 = smooth_blocky(g, 0.05, seed + 1000, n_boxes=3, sigma=2.0)
+    e = standard_normal((2, g.s), seed)
+    return Workload("joint-15x13x6", g, Mag(50000.0, 60.0, 10.0), (m1, m2), (e[0], e[1]))
+
+
 def operator_128(seed: int = 2) -> Workload:
     """128x128 stations, 128x128x32 cells of 50 m; smooth plus blocky models."""
     g = uniform_grid(128, 128, 128, 128, 32, 50.0)

@@ -188,3 +188,34 @@ def test_a_priori_model_and_hard_weights(small, path, anchor):
             assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=tol), (k, i)
     for i in range(2):
         assert rel(m[i], ref.m[i]) <= tol, (i, rel(m[i], ref.m[i]))
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    w = synth.ragged_joint()
+    return (w,) + joint_case(w)
+
+
+@pytest.mark.parametrize("optional", [False, True])
+def test_fast_solver_partial_line_groups(ragged, optional):
+    """13 rows per layer: the 512 kernels' cell-line passes, which take aligned groups
+    of four rows, end every layer with a one-row group.  With and without the
+    optional rows (a-priori model, hard weights), which select different kernels."""
+    gj = lib()
+    w, g, A, dob, sig, wdep = ragged
+    probe = gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512))
+    assert probe.info.fast_path == 1
+    probe.close()
+    kw = dict(KW, kmax=20)
+    extra = {}
+    if optional:
+        extra = dict(m_apr=[synth.smooth_blocky(g, 0.2, seed=31), synth.smooth_blocky(g, 0.02, seed=32)],
+                     w_hard=[synth.uniform_model(g, 0.5, 2.0, seed=33), synth.uniform_model(g, 0.5, 2.0, seed=34)])
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw), **extra)
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=(512, 512), **extra)
+    assert rep["iterations"] == 20
+    for k in (0, 1, 10, 19):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-3), (k, i)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
