@@ -199,8 +199,13 @@ def ragged():
 @pytest.mark.parametrize("optional", [False, True])
 def test_fast_solver_partial_line_groups(ragged, optional):
     """13 rows per layer: the 512 kernels' cell-line passes, which take aligned groups
-    of four rows, end every layer with a one-row group.  With and without the
-    optional rows (a-priori model, hard weights), which select different kernels."""
+    of four rows, end every layer with a one-row group.  With and without hard
+    weights, which select the kernels that read the optional rows.  (An a-priori
+    model is left out here: near m = m_apr the L1 factor of Eq. WL is steep enough to
+    amplify FP32 rounding of m - m_apr, so FP32 solves with one drift from the FP64
+    oracle by up to 1e-2 in 20 iterations on this grid, on the generic kernels as
+    well as these; FP64 keeps 1e-11.  The a-priori model is covered by
+    test_a_priori_model_and_hard_weights.)"""
     gj = lib()
     w, g, A, dob, sig, wdep = ragged
     probe = gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512))
@@ -209,13 +214,12 @@ def test_fast_solver_partial_line_groups(ragged, optional):
     kw = dict(KW, kmax=20)
     extra = {}
     if optional:
-        extra = dict(m_apr=[synth.smooth_blocky(g, 0.2, seed=31), synth.smooth_blocky(g, 0.02, seed=32)],
-                     w_hard=[synth.uniform_model(g, 0.5, 2.0, seed=33), synth.uniform_model(g, 0.5, 2.0, seed=34)])
+        extra = dict(w_hard=[synth.uniform_model(g, 0.5, 2.0, seed=33), synth.uniform_model(g, 0.5, 2.0, seed=34)])
     ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw), **extra)
     m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=(512, 512), **extra)
     assert rep["iterations"] == 20
-    for k in (0, 1, 10, 19):
+    for k in range(20):
         for i in range(2):
-            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-3), (k, i)
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-4), (k, i)
     for i in range(2):
-        assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
+        assert rel(m[i], ref.m[i]) <= 1e-4, (i, rel(m[i], ref.m[i]))
