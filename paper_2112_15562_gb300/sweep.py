@@ -1,7 +1,7 @@
 """Lagrange-parameter sweep (the selection procedure of Secs. 3.1.3 and 5).
 
 The paper runs the joint inversion with fixed (lambda1, lambda2) for a short list of
-increasing pairs and keeps the smallest pair whose models are correlated (judged by
+increasing pairs and keeps the smallest pair whose models are correlated (seen in
 the density-susceptibility cross-plot) and fit both data sets.  Here every pair is
 one solver; all of them advance together in one batched CUDA graph
 (gj_rrcg_batch_*).  Each pair gets its own operators because an operator's
