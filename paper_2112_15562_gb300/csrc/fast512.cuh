@@ -285,7 +285,7 @@ __device__ __forceinline__ void drain(uint64_t *bars, long long t_fail, long lon
 }
 
 // ---------------------------------------------------------------------------
-// Segmentation of the flattened (field, kx, layer) sequence over the warps of a
+// Segmentation of the flattened (kx, field, layer) sequence over the warps of a
 // persistent grid: warp w takes [T w / Wt, T (w+1) / Wt).
 
 __device__ __host__ __forceinline__ long long seg_warps(long long warps, long long T) { return warps < T ? warps : T; }
@@ -306,27 +306,30 @@ struct View2 {  // the two fields of a launch (field 1 unused in single-field la
 };
 
 // ---------------------------------------------------------------------------
-// Item t = (field NC + kx) nz + r of the column passes, set once by division and
-// then advanced by increments.
+// Item t = col nz + r of the column passes, column col = kx nf + fld: the fields
+// alternate column by column, so every warp's segment mixes the cheaper gravity
+// columns (real spectrum) with the magnetic ones.  Set once by division, then
+// advanced by increments.
 struct ColItem {
-    int fld, kx, r;
-    __device__ __forceinline__ void set(int t, int nz) {
-        const int col = t / nz;
+    int fld, kx, r, col;
+    __device__ __forceinline__ void set(int t, int nz, int nf) {
+        col = t / nz;
         r = t - col * nz;
-        fld = col / NC;
-        kx = col - fld * NC;
+        kx = col / nf;
+        fld = col - kx * nf;
     }
-    __device__ __forceinline__ void next(int nz) {
+    __device__ __forceinline__ void next(int nz, int nf) {
         if (++r == nz) {
             r = 0;
-            if (++kx == NC) { kx = 0; ++fld; }
+            ++col;
+            if (++fld == nf) { fld = 0; ++kx; }
         }
     }
 };
 
 // Forward column pass: for each (field, kx), Y = sum_r St_r[kx] . FFT512(Zt_r[kx]),
 // then W[kx][jy] = IFFT512(Y)[jy] for jy < sy.  Persistent warps take balanced
-// contiguous segments of the (field, kx, r) sequence; a column split across warps
+// contiguous segments of the (kx, field, r) sequence; a column split across warps
 // is summed in segment order by the last warp to finish it.
 template <typename R>
 __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const int *done) {
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
     ColItem cu, ci;  // the item being consumed; (lane 0) the next one to issue
-    cu.set(t0, nz);
+    cu.set(t0, nz, V.nfield);
     ci = cu;
     int ti = t0;
     auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
             bulk_load(ts + s * N, op.spec + off * N, TB, &bars[warp][s]);
         }
         ++ti;
-        ci.next(nz);
+        ci.next(nz, V.nfield);
     };
     if (lane == 0)
         while (ti < t1 && ti < t0 + CSTAGES) issue();
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     bool ok = true;
     int t_fail = t1;
     int seg_start = t0;
-    for (int t = t0; t < t1 && ok; ++t, cu.next(nz)) {
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nz, V.nfield)) {
         const int s = (t - t0) % CSTAGES;
         const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
         if (cu.r == nz - 1 || t == t1 - 1) {
             // end of this warp's part of column `col`
             const int fld = cu.fld, kx = cu.kx;
-            const long long col = (long long)fld * NC + kx;
+            const long long col = cu.col;
             const OpView<R> &op = V.op[fld];
             const long long cb = col * nz, ce = cb + nz - 1;
             const bool whole = (seg_start <= cb) && (t == ce);
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
     ColItem cu, ci;  // the item being consumed; (lane 0) the next one to issue
-    cu.set(t0, nz);
+    cu.set(t0, nz, V.nfield);
     ci = cu;
     int ti = t0;
     auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
@@ -510,14 +513,14 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             bulk_load(ts + s * N, V.op[ci.fld].spec + off * N, TB, &bars[warp][s]);
         }
         ++ti;
-        ci.next(nz);
+        ci.next(nz, V.nfield);
     };
     if (lane == 0)
         while (ti < t1 && ti < t0 + CSTAGES) issue();
     C vh[16];
     bool ok = true;
     int t_fail = t1;
-    for (int t = t0; t < t1 && ok; ++t, cu.next(nz)) {
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nz, V.nfield)) {
         const int r = cu.r, fld = cu.fld, kx = cu.kx;
         const OpView<R> &op = V.op[fld];
         if (t == t0 || r == 0) {  // a new column

@@ -193,7 +193,7 @@ bool fast_eligible(const gj_op *op) {
 }
 
 // Largest number of warps that share one (field, kx) column when the persistent
-// column kernels split the (field, kx, layer) sequence into balanced segments.
+// column kernels split the (kx, field, layer) sequence into balanced segments.
 int fast_slots(int nfield, int nz, int grid_ctas) {
     const long long T = (long long)nfield * 257 * nz;
     const long long Wt = std::min((long long)grid_ctas * f512::CWARPS, T);
