@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
 // ---------------------------------------------------------------------------
 // Persistent joint row passes (both fields in one complex transform per line).
 // A team of four warps takes a balanced contiguous range of the aligned four-line
-// groups of the layers (warp k of the team transforms line 4q + k of group q), so
-// that no launch ends in a partial wave.  The half spectra of a group sit in a
+// groups of the layers (a layer's last group may hold fewer lines; warp k of the
+// team transforms line k of each group), so that no launch ends in a partial wave.  The half spectra of a group sit in a
 // double-buffered team tile stage[field][slot][kq(kx)] and move to or from the
 // transposed layout out[r][kx][iy] as whole 32-byte sectors (four lines of one
 // column).  kq puts even columns first and odd ones from 136 on; with the slot
