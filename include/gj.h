@@ -140,9 +140,8 @@ gj_status gj_gramian_value_grad(int64_t n, gj_precision precision,
 
 /*
  * gj_gramian_value_grad_noalloc - the same outputs as gj_gramian_value_grad,
- * for callers that must not allocate device memory: code running under a CUDA
- * stream capture that may not create allocations, hosts whose device memory is
- * owned by another allocator (a framework's caching pool, a fixed arena), or
+ * for callers that must not allocate device memory: hosts whose device memory
+ * is owned by another allocator (a framework's caching pool, a fixed arena), or
  * real-time loops that forbid allocation.  (The paper has no counterpart; this
  * is an interface for such callers.)
  *

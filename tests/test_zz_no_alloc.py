@@ -1,7 +1,7 @@
 """The allocation-free Gramian entry point (gj_gramian_value_grad_noalloc).
 
-Some callers cannot allocate device memory: code inside a CUDA stream capture,
-hosts whose memory belongs to another allocator, loops that forbid allocation.
+Some callers cannot allocate device memory: hosts whose memory belongs to
+another allocator, loops that forbid allocation.
 This entry point serves them with a fixed scratch array inside the library.
 The test calls it through the C ABI with buffers allocated beforehand and checks
 two calls in a row (different sizes and data, so stale scratch from the first
