@@ -267,22 +267,27 @@ __global__ void __launch_bounds__(256) k_col_adj(OpView<R> op0, OpView<R> op1, i
 // ---------------------------------------------------------------------------
 // Plain functors.
 
+// row length of the staged functor rows of the 512 row passes (pre[a][i][kStageRow])
+constexpr int kStageRow = 256;
+
 template <typename R>
 struct LoadPlain {  // a = x0[la*pitch + j], b = x1[lb*pitch + j]
     const R *x0;
     const R *x1;
     int pitch;
+    static constexpr int NPRE = 1;  // rows la of x0 and lb of x1, staged by the 512 team passes
+    __device__ const R *pre_src(int, int i) const { return i == 0 ? x0 : x1; }
     __device__ void init() {}
     __device__ __forceinline__ void fetch(int la, int lb, bool hb, int j, R &a, R &b) const {
         a = x0[(size_t)la * pitch + j];
         b = hb ? x1[(size_t)lb * pitch + j] : R(0);
     }
     // elements j0 + k * stride (k < K) below n; zero beyond
-    template <int K>
+    template <int K, bool PRE = false>
     __device__ __forceinline__ void fetch_batch(int la, int lb, bool hb, int j0, int stride, int n, R (&a)[K],
-                                                R (&b)[K]) const {
-        const R *pa = x0 + (size_t)la * pitch;
-        const R *pb = x1 + (size_t)lb * pitch;
+                                                R (&b)[K], const R *pre = nullptr) const {
+        const R *pa = PRE ? pre : x0 + (size_t)la * pitch;
+        const R *pb = PRE ? pre + kStageRow : x1 + (size_t)lb * pitch;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;
@@ -298,15 +303,17 @@ struct StorePlain {
     R *y0;
     R *y1;
     int pitch;
+    static constexpr int NPRE = 0;  // reads nothing
+    __device__ const R *pre_src(int, int) const { return nullptr; }
     __device__ __forceinline__ void prefetch(int, int, bool, int, int) const {}
     __device__ void init() {}
     __device__ __forceinline__ void store(int la, int lb, bool hb, int j, R a, R b) const {
         y0[(size_t)la * pitch + j] = a;
         if (hb) y1[(size_t)lb * pitch + j] = b;
     }
-    template <int K>
+    template <int K, bool PRE = false>
     __device__ __forceinline__ void store_batch(int la, int lb, bool hb, int j0, int stride, int n, const R (&a)[K],
-                                                const R (&b)[K]) const {
+                                                const R (&b)[K], const R * = nullptr) const {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int j = j0 + k * stride;

@@ -227,20 +227,30 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
 }
 
 // ---------------------------------------------------------------------------
-// Persistent joint row passes (both fields in one complex transform per line).
-// A team of four warps takes a balanced contiguous range of the aligned four-line
-// groups of the layers (a layer's last group may hold fewer lines; warp k of the
-// team transforms line k of each group), so that no launch ends in a partial wave.  The half spectra of a group sit in a
-// double-buffered team tile stage[field][slot][kq(kx)] and move to or from the
-// transposed layout out[r][kx][iy] as whole 32-byte sectors (four lines of one
-// column).  kq puts even columns first and odd ones from 136 on; with the slot
-// stride LS = 274 (2 mod 16), a half-warp's 16 consecutive columns of one line, and
-// its 4 x 4 (column, slot) pairs of a group, each fall in 16 distinct bank pairs.
-// One named barrier per group and team.  The rows the functor reads in every
-// launch (m, p, l) are staged one line ahead with asynchronous copies.
+// Persistent row passes in teams of four warps.  A team takes a balanced contiguous
+// range of the aligned groups of the layers (a layer's last group may hold fewer
+// lines), so that no launch ends in a partial wave.  Two modes:
+//   joint: both fields of a line in one complex transform; a group is four lines,
+//          warp k takes line k; the tile is stage[field][slot < 4][kq(kx)] with slot
+//          stride 274 (2 mod 16);
+//   pair:  one field, two lines per transform (warp k: lines 2k and 2k + 1); a group
+//          is eight lines; the tile is stage[slot < 8][kq(kx)] with slot stride 273
+//          (1 mod 16).
+// The half spectra of a group sit in a double-buffered team tile and move to or from
+// the transposed layout out[r][kx][iy] as whole 32-byte sectors.  kq puts even
+// columns first and odd ones from 136 on; with these strides a half-warp's 16
+// consecutive columns of one slot, and its (column, slot) pairs of a group store or
+// load, each fall in 16 distinct bank pairs.  One named barrier per group and team.
+// The functor rows read in every launch are staged one transform ahead with
+// asynchronous copies.
 
-constexpr int TEAM = 4;                 // warps per team = lines per group
-constexpr int LS = 274, FS = TEAM * LS;  // slot and field strides of a team tile (complex words)
+constexpr int TEAM = 4;                  // warps per team
+constexpr int LS = 274, FS = TEAM * LS;  // joint tile: slot and field strides (complex words)
+constexpr int LSP = 273;                 // pair tile: slot stride (8 slots fit in 2 FS)
+template <bool PAIR> struct TeamMode {
+    static constexpr int LPG = PAIR ? 2 * TEAM : TEAM;  // lines per group
+    static constexpr int GPT = PAIR ? 8 : 4;            // slots one thread row of a store covers
+};
 
 __device__ __forceinline__ void team_barrier(int team) {  // barrier 0 stays with __syncthreads
     asm volatile("bar.sync %0, %1;\n" ::"r"(1 + team), "r"(TEAM * 32) : "memory");
@@ -250,14 +260,13 @@ __device__ __forceinline__ int kq(int kx) { return (kx & 1) ? 136 + (kx >> 1) : 
 
 // Z = FFT(a + i b) in the lane layout (v[k1] = Z[lambda + 32 k1]) -> the half
 // spectra A = (Z[kx] + conj Z[N - kx]) / 2 and B = (Z[kx] - conj Z[N - kx]) / 2i,
-// kx = 0..256, into slot g of a team tile.  For lambda != 0, Z[N - kx] sits in
+// kx = 0..256, at sa[kq(kx)] and sb[kq(kx)].  For lambda != 0, Z[N - kx] sits in
 // lane (h, 16 - l - h) at k1' = 15 - k1; lane 0 (lambda = 0) holds it at 16 - k1.
 template <typename R>
-__device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *stage, int g) {
+__device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *sa, cpx<R> *sb) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int partner = h ? 31 - l : ((16 - l) & 15);
-    C *sa = stage + g * LS, *sb = sa + FS;
     const int q0 = h * 136 + l;  // kq(lambda + 32 k1) = q0 + 16 k1
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) {
@@ -275,52 +284,55 @@ __device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *st
     }
 }
 
-// Slot g < ng of a team tile -> oa[kx * H + g], ob[kx * H + g]; the team's 128
-// threads each take (g, kx) = (tid % 4, tid / 4 + 32 i).
-template <typename R>
+// Slots g < ng of a team tile -> out[kx * H + g] (joint: field 0 to oa, field 1 to
+// ob; pair: eight slots to oa).  The team's 128 threads take (g, kx) =
+// (tid % GPT, tid / GPT + (128 / GPT) i): kx advances by 32 or 16, keeping its parity,
+// so kq(kx) advances by half of that.
+template <typename R, bool PAIR>
 __device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid) {
-    const int g = tid % TEAM;
+    constexpr int GPT = TeamMode<PAIR>::GPT, KS = 128 / GPT;
+    const int g = tid % GPT;
     if (g >= ng) return;
-    // kx += 32 keeps its parity, so kq(kx) advances by 16
-    int kx = tid / TEAM;
-    const cpx<R> *sa = stage + g * LS + kq(kx);
+    int kx = tid / GPT;
+    const cpx<R> *sa = stage + g * (PAIR ? LSP : LS) + kq(kx);
     size_t o = (size_t)kx * H + g;
-    for (; kx < NC; kx += 32, sa += 16, o += 32 * H) {
+    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * H) {
         oa[o] = sa[0];
-        ob[o] = sa[FS];
+        if (!PAIR) ob[o] = sa[FS];
     }
 }
 
-// ia[kx * H + g], ib[kx * H + g] -> slot g < ng of a team tile (asynchronous copies).
-template <typename R>
+// in[kx * H + g] -> slots g < ng of a team tile (asynchronous copies; layout as in
+// team_store).
+template <typename R, bool PAIR>
 __device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid) {
-    const int g = tid % TEAM;
+    constexpr int GPT = TeamMode<PAIR>::GPT, KS = 128 / GPT;
+    const int g = tid % GPT;
     if (g >= ng) return;
-    int kx = tid / TEAM;  // as in team_store
-    cpx<R> *sa = stage + g * LS + kq(kx);
+    int kx = tid / GPT;
+    cpx<R> *sa = stage + g * (PAIR ? LSP : LS) + kq(kx);
     size_t o = (size_t)kx * H + g;
-    for (; kx < NC; kx += 32, sa += 16, o += 32 * H) {
+    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * H) {
         cp_async8(sa, ia + o);
-        cp_async8(sa + FS, ib + o);
+        if (!PAIR) cp_async8(sa + FS, ib + o);
     }
 }
 
-// Slot g of a team tile (A + i B, Hermitian-extended) -> inverse transform ->
-// y[lane + 32 i] in a[i] + i b[i].
+// A at sa, B at sb (B taken as zero when has_b is false; Hermitian-extended A + i B)
+// -> inverse transform -> y[lane + 32 i] in a[i] + i b[i].
 template <typename R, class TW>
-__device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R> *buf, const TW &tw,
-                                               R (&a)[8], R (&b)[8]) {
+__device__ __forceinline__ void stage_to_lines(const cpx<R> *sa, const cpx<R> *sb, bool has_b, cpx<R> *buf,
+                                               const TW &tw, R (&a)[8], R (&b)[8]) {
     using C = cpx<R>;
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int lam = 2 * l + h;
-    const C *sa = stage + g * LS, *sb = sa + FS;
     C v[16];
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) {
         const int k = lam + 32 * k1;
         const bool lo = k <= H;
         const int kk = lo ? k : N - k;
-        C A = sa[kq(kk)], B = sb[kq(kk)];
+        C A = sa[kq(kk)], B = has_b ? sb[kq(kk)] : czero<C>();
         if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
         v[k1] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
     }
@@ -338,10 +350,11 @@ __device__ __forceinline__ void stage_to_lines(const cpx<R> *stage, int g, cpx<R
     }
 }
 
-// Stages the functor's rows of line t (n elements each) into pre[a][field][H]: 16-byte
-// copies where the rows allow them, else 4-byte ones.  Does not commit.
+// Stages the functor's rows into pre[a][i][H] (n elements each): source i = 0 from
+// row ta, i = 1 from row tb (skipped when tb < 0); 16-byte copies where the rows
+// allow them, else 4-byte ones.  Does not commit.
 template <typename R, class Fn>
-__device__ __forceinline__ void prefetch_rows(const Fn &fn, R *pre, int t, int n) {
+__device__ __forceinline__ void prefetch_rows(const Fn &fn, R *pre, int ta, int tb, int n) {
     constexpr int V4 = 16 / sizeof(R);
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -349,7 +362,8 @@ __device__ __forceinline__ void prefetch_rows(const Fn &fn, R *pre, int t, int n
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const R *src = fn.pre_src(a, i);
-            if (!src) continue;
+            const int t = i == 0 ? ta : tb;
+            if (!src || t < 0) continue;
             src += (size_t)t * n;
             R *dst = pre + (a * 2 + i) * H;
             if (n % V4 == 0 && ((uintptr_t)src & 15) == 0) {
@@ -376,21 +390,33 @@ constexpr int row_t_words() {
     return (NW / TEAM) * 2 * 2 * FS + NW * row_warp_words<R, NPRE>();
 }
 
-// Group q of a layer-major sequence (gpl groups per layer): layer, first line.
-__device__ __forceinline__ void group_lines(int q, int gpl, int lpl, int &r, int &iy0, int &ng) {
+// Group q of a layer-major sequence (gpl groups of lpg lines per layer): layer, first
+// line, lines in the group.
+__device__ __forceinline__ void group_lines(int q, int gpl, int lpl, int lpg, int &r, int &iy0, int &ng) {
     r = q / gpl;
-    iy0 = (q - r * gpl) * TEAM;
-    ng = min(TEAM, lpl - iy0);
+    iy0 = (q - r * gpl) * lpg;
+    ng = min(lpg, lpl - iy0);
 }
 
-// Forward joint row pass: line r lpl + iy of both fields (through the prologue
-// functor) -> half spectra out[r][kx][iy].
-template <typename R, class Pro, int NW>
+// Warp k's transform in a group (layer r, first line iy0, ng lines): its lines la
+// (always) and lb (when hb), active when the group reaches la.
+template <bool PAIR>
+__device__ __forceinline__ bool warp_lines(int k, int r, int iy0, int ng, int lpl, int &la, int &lb, bool &hb) {
+    const int s = PAIR ? 2 * k : k;
+    la = r * lpl + iy0 + s;
+    lb = PAIR ? la + 1 : la;
+    hb = PAIR ? s + 1 < ng : true;
+    return s < ng;
+}
+
+// Forward row pass: lines r lpl + iy (both fields, or pairs of one field's lines)
+// through the prologue functor -> half spectra out[r][kx][iy].
+template <typename R, class Pro, int NW, bool PAIR>
 __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, int lpl, int n_in, int out_sel,
                                                             Pro pro, const int *done) {
     using C = cpx<R>;
     static_assert(NW % TEAM == 0, "whole teams");
-    constexpr int NT = NW / TEAM;
+    constexpr int NT = NW / TEAM, LPG = TeamMode<PAIR>::LPG;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -402,61 +428,64 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, 
     pro.init();
     LaneTw<R> tw;
     tw.load_fwd(V.op[0].twx);
-    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const int gpl = (lpl + LPG - 1) / LPG;
     const long long NG = (long long)nz * gpl;
     const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
     const long long tm = (long long)blockIdx.x * NT + team;
     if (tm < Tt) {
         const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         C *out0 = sel_buf(V.op[0], out_sel), *out1 = sel_buf(V.op[1], out_sel);
-        int r, iy0, ng;
-        group_lines(q0, gpl, lpl, r, iy0, ng);
-        if (k < ng) prefetch_rows(pro, pre, r * lpl + iy0 + k, n_in);
+        int r, iy0, ng, la, lb;
+        bool hb;
+        group_lines(q0, gpl, lpl, LPG, r, iy0, ng);
+        if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) prefetch_rows(pro, pre, la, hb ? lb : -1, n_in);
         cp_async_commit();
         for (int q = q0; q < q1; ++q) {
-            group_lines(q, gpl, lpl, r, iy0, ng);
+            group_lines(q, gpl, lpl, LPG, r, iy0, ng);
             C *tile = tiles + (q & 1) * 2 * FS;
-            const bool act = k < ng;  // this warp has a line in group q
+            const bool act = warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb);  // this warp has a transform in q
             R a[8], b[8];
             if (act) {
-                const int t = r * lpl + iy0 + k;
                 cp_async_wait<0>();
                 __syncwarp();
                 R a0[4], b0[4], a1[4], b1[4];
-                pro.template fetch_batch<4, true>(t, t, true, lane, 32, n_in, a0, b0, pre);
-                pro.template fetch_batch<4, true>(t, t, true, lane + 128, 32, n_in, a1, b1, pre);
+                pro.template fetch_batch<4, true>(la, lb, hb, lane, 32, n_in, a0, b0, pre);
+                pro.template fetch_batch<4, true>(la, lb, hb, lane + 128, 32, n_in, a1, b1, pre);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
                 __syncwarp();
             }
-            if (q + 1 < q1) {  // the rows of this warp's line in the next group
-                int r2, iy2, ng2;
-                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
-                if (k < ng2) prefetch_rows(pro, pre, r2 * lpl + iy2 + k, n_in);
+            if (q + 1 < q1) {  // the rows of this warp's transform in the next group
+                int r2, iy2, ng2, la2, lb2;
+                bool hb2;
+                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
+                if (warp_lines<PAIR>(k, r2, iy2, ng2, lpl, la2, lb2, hb2))
+                    prefetch_rows(pro, pre, la2, hb2 ? lb2 : -1, n_in);
             }
             cp_async_commit();
             if (act) {
                 C v[16];
                 fwd512_from_lines<R>(a, b, buf, tw, v);
-                split_to_stage<R>(v, tile, k);
+                if (PAIR) split_to_stage<R>(v, tile + 2 * k * LSP, tile + (2 * k + 1) * LSP);
+                else split_to_stage<R>(v, tile + k * LS, tile + FS + k * LS);
             }
             team_barrier(team);  // the group's tile is complete; the other tile is free again
             const size_t off = (size_t)r * NC * H + iy0;
-            team_store<R>(tile, out0 + off, out1 + off, ng, tid);
+            team_store<R, PAIR>(tile, out0 + off, out1 + off, ng, tid);
         }
     }
     pro.flush(red);
 }
 
-// Inverse joint row pass: half spectra in[r][kx][iy] -> line r lpl + iy of both
-// fields, cropped to n_out, through the epilogue functor.  Copy groups in flight
-// at the top of group q: [tile of q], [rows of q's line].
-template <typename R, class Epi, int NW>
+// Inverse row pass: half spectra in[r][kx][iy] -> lines r lpl + iy (both fields, or
+// pairs of one field's lines), cropped to n_out, through the epilogue functor.  Copy
+// groups in flight at the top of group q: [tile of q], [rows of q's transform].
+template <typename R, class Epi, int NW, bool PAIR>
 __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, int lpl, int n_out, int in_sel,
                                                             Epi epi, const int *done) {
     using C = cpx<R>;
     static_assert(NW % TEAM == 0, "whole teams");
-    constexpr int NT = NW / TEAM;
+    constexpr int NT = NW / TEAM, LPG = TeamMode<PAIR>::LPG;
     if (stopped(done)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -468,50 +497,54 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, 
     epi.init();
     LaneTw<R> tw;
     tw.load_inv(V.op[0].twx);
-    const int gpl = (lpl + TEAM - 1) / TEAM;
+    const int gpl = (lpl + LPG - 1) / LPG;
     const long long NG = (long long)nz * gpl;
     const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
     const long long tm = (long long)blockIdx.x * NT + team;
     if (tm < Tt) {
         const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         const C *in0 = sel_buf(V.op[0], in_sel), *in1 = sel_buf(V.op[1], in_sel);
-        int r, iy0, ng;
-        group_lines(q0, gpl, lpl, r, iy0, ng);
+        int r, iy0, ng, la, lb;
+        bool hb;
+        group_lines(q0, gpl, lpl, LPG, r, iy0, ng);
         {
             const size_t off = (size_t)r * NC * H + iy0;
-            team_load<R>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid);
+            team_load<R, PAIR>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid);
             cp_async_commit();
-            if (k < ng) prefetch_rows(epi, pre, r * lpl + iy0 + k, n_out);
+            if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) prefetch_rows(epi, pre, la, hb ? lb : -1, n_out);
             cp_async_commit();
         }
         for (int q = q0; q < q1; ++q) {
-            group_lines(q, gpl, lpl, r, iy0, ng);
+            group_lines(q, gpl, lpl, LPG, r, iy0, ng);
             cp_async_wait<1>();  // this thread's copies of the tile of q
             team_barrier(team);  // everyone's copies of q; the other tile is free again
             if (q + 1 < q1) {
                 int r2, iy2, ng2;
-                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
+                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
                 const size_t off = (size_t)r2 * NC * H + iy2;
-                team_load<R>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid);
+                team_load<R, PAIR>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid);
             }
             cp_async_commit();
-            if (k < ng) {
-                const int t = r * lpl + iy0 + k;
+            if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) {
+                const C *tile = tiles + (q & 1) * 2 * FS;
                 R a[8], b[8];
-                stage_to_lines<R>(tiles + (q & 1) * 2 * FS, k, buf, tw, a, b);
-                cp_async_wait<1>();  // the rows of line t
+                if (PAIR) stage_to_lines<R>(tile + 2 * k * LSP, tile + (2 * k + 1) * LSP, hb, buf, tw, a, b);
+                else stage_to_lines<R>(tile + k * LS, tile + FS + k * LS, true, buf, tw, a, b);
+                cp_async_wait<1>();  // the rows of this transform
                 __syncwarp();
                 R a0[4], b0[4], a1[4], b1[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
-                epi.template store_batch<4, true>(t, t, true, lane, 32, n_out, a0, b0, pre);
-                epi.template store_batch<4, true>(t, t, true, lane + 128, 32, n_out, a1, b1, pre);
+                epi.template store_batch<4, true>(la, lb, hb, lane, 32, n_out, a0, b0, pre);
+                epi.template store_batch<4, true>(la, lb, hb, lane + 128, 32, n_out, a1, b1, pre);
                 __syncwarp();
             }
             if (q + 1 < q1) {
-                int r2, iy2, ng2;
-                group_lines(q + 1, gpl, lpl, r2, iy2, ng2);
-                if (k < ng2) prefetch_rows(epi, pre, r2 * lpl + iy2 + k, n_out);
+                int r2, iy2, ng2, la2, lb2;
+                bool hb2;
+                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
+                if (warp_lines<PAIR>(k, r2, iy2, ng2, lpl, la2, lb2, hb2))
+                    prefetch_rows(epi, pre, la2, hb2 ? lb2 : -1, n_out);
             }
             cp_async_commit();
         }

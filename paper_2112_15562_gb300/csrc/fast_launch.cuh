@@ -38,13 +38,13 @@ template <typename R, class Epi, int NW>
 inline void set_row_resid_attr() {
     allow_max_smem(k_row_resid512<R, Epi, NW>);
 }
-template <typename R, class Pro>
+template <typename R, class Pro, bool PAIR = false>
 inline void set_row_fwd_t_attr() {
-    allow_max_smem(k_row_fwd512t<R, Pro, kRowNW>);
+    allow_max_smem(k_row_fwd512t<R, Pro, kRowNW, PAIR>);
 }
-template <typename R, class Epi>
+template <typename R, class Epi, bool PAIR = false>
 inline void set_row_inv_t_attr() {
-    allow_max_smem(k_row_inv512t<R, Epi, kRowNW>);
+    allow_max_smem(k_row_inv512t<R, Epi, kRowNW, PAIR>);
 }
 template <typename R>
 inline void set_col_attr() {
@@ -75,17 +75,18 @@ inline void row_resid(const View2<R> &V, int nlines, int n_out, const Epi &epi, 
                                                                                                  done);
 }
 
-// persistent joint row passes over nz layers of lpl lines (grid: one CTA per SM)
-template <typename R, class Pro>
+// persistent team row passes over nz layers of lpl lines (grid: one CTA per SM);
+// PAIR: one field, two of its lines per transform; else both fields, one line each
+template <typename R, bool PAIR = false, class Pro>
 inline void row_fwd_t(const View2<R> &V, int grid, int nz, int lpl, int n_in, int out_sel, const Pro &pro,
                       const int *done, cudaStream_t st) {
-    k_row_fwd512t<R, Pro, kRowNW><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Pro::NPRE>(), st>>>(
+    k_row_fwd512t<R, Pro, kRowNW, PAIR><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Pro::NPRE>(), st>>>(
         V, nz, lpl, n_in, out_sel, pro, done);
 }
-template <typename R, class Epi>
+template <typename R, bool PAIR = false, class Epi>
 inline void row_inv_t(const View2<R> &V, int grid, int nz, int lpl, int n_out, int in_sel, const Epi &epi,
                       const int *done, cudaStream_t st) {
-    k_row_inv512t<R, Epi, kRowNW><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Epi::NPRE>(), st>>>(
+    k_row_inv512t<R, Epi, kRowNW, PAIR><<<grid, kRowNW * 32, smem_row_t<R, kRowNW, Epi::NPRE>(), st>>>(
         V, nz, lpl, n_out, in_sel, epi, done);
 }
 

@@ -66,10 +66,10 @@ static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
 static void fast_forward(const gj_op *o, const float *m, float *d, cudaStream_t st) {
     using namespace f512;
     View2<float> V = make_view2<float>(o, nullptr);
-    set_row_fwd_attr<float, LoadPlain<float>, kCellNW, kCellFPW>();
+    set_row_fwd_t_attr<float, LoadPlain<float>, true>();
     set_row_inv_attr<float, StorePlain<float>, kDataNW, kDataFPW>();
     set_col_attr<float>();
-    row_fwd<float, kCellNW, kCellFPW>(V, 0, o->nz * o->ny, o->ny, o->nx, 0, LoadPlain<float>{m, m, o->nx}, nullptr, st);
+    row_fwd_t<float, true>(V, o->col_grid, o->nz, o->ny, o->nx, 0, LoadPlain<float>{m, m, o->nx}, nullptr, st);
     col_fwd<float>(V, o->col_grid, nullptr, st);
     row_inv<float, kDataNW, kDataFPW>(V, 0, o->sy, o->sy, o->sx, 1, StorePlain<float>{d, d, o->sx}, nullptr, st);
 }
@@ -78,11 +78,11 @@ static void fast_adjoint(const gj_op *o, const float *r, float *g, cudaStream_t 
     using namespace f512;
     View2<float> V = make_view2<float>(o, nullptr);
     set_row_fwd_attr<float, LoadPlain<float>, kDataNW, kDataFPW>();
-    set_row_inv_attr<float, StorePlain<float>, kCellNW, kCellFPW>();
+    set_row_inv_t_attr<float, StorePlain<float>, true>();
     set_col_attr<float>();
     row_fwd<float, kDataNW, kDataFPW>(V, 0, o->sy, o->sy, o->sx, 2, LoadPlain<float>{r, r, o->sx}, nullptr, st);
     col_adj<float>(V, o->col_grid, nullptr, st);
-    row_inv<float, kCellNW, kCellFPW>(V, 0, o->nz * o->ny, o->ny, o->nx, 0, StorePlain<float>{g, g, o->nx}, nullptr, st);
+    row_inv_t<float, true>(V, o->col_grid, o->nz, o->ny, o->nx, 0, StorePlain<float>{g, g, o->nx}, nullptr, st);
 }
 
 gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {
