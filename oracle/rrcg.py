@@ -99,15 +99,18 @@ def rrcg_joint(fwd: Sequence[Callable], adj: Sequence[Callable], d_obs, sigma, m
             for i in range(nf):
                 if not sat[i]:
                     alpha[i] = max(P.q[i] * alpha[i], P.alpha_min[i])
-        rec = {"k": k, "phi": phi, "alpha": list(alpha), "S_G": gramian(m[0], m[1]),
+        # W_k from m_k (Eq. W, Eq. WL)
+        W = [ws[i] * lp_weight(m[i], mapr[i], P.eps2, P.p[i]) for i in range(nf)]
+        mt = [W[i] * m[i] for i in range(nf)]
+        # S_G of the original models, and of the models in the Gramian's space
+        # (Appendix A: the weighted-space Gramian of W m)
+        sg_space = gramian(m[0], m[1]) if P.gramian_space == "original" else gramian(mt[0], mt[1])
+        rec = {"k": k, "phi": phi, "alpha": list(alpha), "S_G": gramian(m[0], m[1]), "S_G_space": sg_space,
                "satisfied": list(sat)}
         hist.append(rec)
         if (P.stop_on_chi2 and all(sat)) or k >= P.kmax:
             break
 
-        # W_k from m_k (Eq. W, Eq. WL)
-        W = [ws[i] * lp_weight(m[i], mapr[i], P.eps2, P.p[i]) for i in range(nf)]
-        mt = [W[i] * m[i] for i in range(nf)]
         if P.anchor == "apriori":
             anchor = [W[i] * mapr[i] for i in range(nf)]
         else:
@@ -157,13 +160,3 @@ def rrcg_joint(fwd: Sequence[Callable], adj: Sequence[Callable], d_obs, sigma, m
 
     return RRCGResult(m=m, iterations=k, converged=all(sat), satisfied=list(sat), history=hist)
 
-
-def objective(A, m, d_obs, sigma, alpha, W, lam, m_apr=None):
-    """Eq. (GlobalFunction1) with per-field Lagrange weights applied to S_G:
-    sum_i ||W_d (A m - d)||^2 + alpha_i ||W (m - m_apr)||^2 + (lam_1 + lam_2)/2 S_G."""
-    tot = 0.0
-    for i in range(2):
-        r = (A[i] @ m[i] - d_obs[i]) / sigma[i]
-        ma = 0.0 if m_apr is None else m_apr[i]
-        tot += r @ r + alpha[i] * np.sum((W[i] * (m[i] - ma)) ** 2)
-    return tot + 0.5 * (lam[0] + lam[1]) * gramian(m[0], m[1])
