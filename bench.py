@@ -150,6 +150,17 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+def depth_weights(z_edges, beta: float):
+    """The caller's depth weighting, an input of the solver: (z_c / z_c,top)^(-beta/2) at
+    the layer centres (the Li & Oldenburg form, which the paper names without printing
+    its exponent; the top layer has weight 1)."""
+    import numpy as np
+
+    z = np.asarray(z_edges, dtype=np.float64)
+    zc = 0.5 * (z[:-1] + z[1:])
+    return (zc / zc[0]) ** (-beta / 2.0)
+
+
 def reduce_max_ms(total_ms: float, dist, device) -> float:
     """The timed region's length as the maximum over ranks (no-op on one rank)."""
     if dist is None:
@@ -178,7 +189,7 @@ def build_problem(gj, torch, prec, dev):
     d_ex = [ops[i].forward(m_true[i]) for i in range(2)]
     sigma = [0.01 * d.abs() + 0.01 * d.abs().max() for d in d_ex]
     dobs = [d_ex[i] + sigma[i] * torch.from_numpy(w.noise[i]).to(dt).to(dev) for i in range(2)]
-    wdep = [torch.from_numpy(gj.depth_weights(g.z_edges, b)).to(dt).to(dev) for b in (2.0, 3.0)]
+    wdep = [torch.from_numpy(depth_weights(g.z_edges, b)).to(dt).to(dev) for b in (2.0, 3.0)]
     return w, g, ops, dobs, sigma, wdep
 
 
@@ -403,7 +414,7 @@ def batched_leg(gj, torch, dev, flush, steps=20, warmup=3):
         sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
         rng = np.random.default_rng(40 + i)
         dob = [d[k] + sig[k] * torch.from_numpy(rng.standard_normal(gr.s)).float().to(dev) for k in range(2)]
-        wd = [torch.from_numpy(gj.depth_weights(gr.z_edges, b)).float().to(dev) for b in (2.0, 3.0)]
+        wd = [torch.from_numpy(depth_weights(gr.z_edges, b)).float().to(dev) for b in (2.0, 3.0)]
         m = [torch.zeros(gr.n, device=dev) for _ in range(2)]
         P = gj.solver_params(p=(1, 1), lam=(2.0, 100.0), kmax=steps + warmup + 4, stop_on_chi2=False)
         solvers.append(gj.Solver(ops, P, dob, sig, wd, m))
@@ -464,7 +475,7 @@ def paper_shapes_leg(gj, torch, dev, flush, steps=20, warmup=3):
         sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
         rng = np.random.default_rng(7)
         dob = [d[k] + sig[k] * torch.from_numpy(rng.standard_normal(gr.s)).float().to(dev) for k in range(2)]
-        wd = [torch.from_numpy(gj.depth_weights(gr.z_edges, b)).float().to(dev) for b in (2.0, 3.0)]
+        wd = [torch.from_numpy(depth_weights(gr.z_edges, b)).float().to(dev) for b in (2.0, 3.0)]
         sv, m, P = solver_for(gj, torch, ops, gr, dob, sig, wd, steps + warmup + 4, dev)
         ts, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
         sv.close()

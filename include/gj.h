@@ -112,11 +112,42 @@ gj_status gj_op_info(const gj_op *op, gj_op_info_t *info);
 void gj_op_destroy(gj_op *op);
 
 /*
+ * gj_op_status - reads the operator's device error word (synchronises
+ * `stream`).  Returns GJ_OK if no bounded wait of its kernels has given up,
+ * else the recorded status (GJ_ERR_TIMEOUT).  With reset = 1 a recorded error
+ * is also cleared together with the layer-sum arrival counters, which makes
+ * the operator usable again; the products computed while it was set are not
+ * repaired.  Operators off the fast path never wait and always return GJ_OK.
+ * (A library safeguard; the paper has no counterpart.)
+ */
+gj_status gj_op_status(gj_op *op, int reset, gj_stream_t stream);
+
+/*
+ * gj_selftest_bounded_wait - runs the library's bounded mbarrier wait on a
+ * barrier that nothing ever completes, giving up after limit_ns nanoseconds
+ * (0 <= limit_ns <= 1e10), and returns the status the kernel recorded:
+ * GJ_ERR_TIMEOUT when the bound works.  No copy is in flight, so nothing can
+ * land after the wait gives up, and the context stays usable.  Synchronous;
+ * allocates one int of device memory.  (A diagnostic of the failure path; the
+ * paper has no counterpart.)
+ */
+gj_status gj_selftest_bounded_wait(int64_t limit_ns, gj_stream_t stream);
+
+/*
  * gj_g_forward - d = A m for one field (Eq. d=gm): the sum over depth layers
  * of IFFT2(FFT2(T_r) . FFT2(X_r)) cropped to the station block, where X_r is
  * layer r of m in the upper-left corner of an Ny x Nx zero array
  * (Sec. 2.7.1).  m: n values, d: s values, both of the op's precision;
  * m and d must not overlap.
+ *
+ * Device-side failures (this and gj_g_adjoint): on the 512 x 512 fast path the
+ * column kernels wait on their bulk copies with a bound (200 ms per wait).  A
+ * wait that gives up records GJ_ERR_TIMEOUT in the operator's error word and
+ * leaves d (or g) incomplete; every later fast-path column launch of that
+ * operator then returns at once (the operator is unusable) until
+ * gj_op_status(op, 1, ...) reads and clears the word.  The call itself has
+ * already returned GJ_OK by then, so check gj_op_status after products whose
+ * results matter.
  */
 gj_status gj_g_forward(const gj_op *op, const void *m, void *d, gj_stream_t stream);
 
@@ -150,7 +181,9 @@ gj_status gj_gramian_value_grad(int64_t n, gj_precision precision,
  * which every GPU that loads the library holds until the process exits.  The
  * first call on each device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current); make that first call before
- * any stream capture.  Limit: n <= 16,777,216; larger n returns GJ_ERR_ARG
+ * any stream capture.  The address is kept per device index for the life of
+ * the process: a caller that resets a device (cudaDeviceReset) must not call
+ * this entry point on that device again.  Limit: n <= 16,777,216; larger n returns GJ_ERR_ARG
  * (use gj_gramian_value_grad).  All calls on a device share the array, which
  * keeps the last call's contents; every slot a call reads is written earlier
  * in the same call, so nothing needs clearing.  Calls that overlap on the GPU
@@ -187,7 +220,9 @@ typedef struct {
 } gj_rrcg_params;
 
 typedef struct {
-    int status;            /* GJ_OK or GJ_ERR_NONFINITE */
+    int status;            /* GJ_OK, GJ_ERR_NONFINITE (a non-finite misfit or step length
+                              stopped the solve) or GJ_ERR_TIMEOUT (a bounded wait of the
+                              gravity operator's column kernels gave up; see gj_op_status) */
     int iterations;        /* model updates performed */
     int converged;         /* 1 if both fields passed Eq. chi2 */
     int satisfied[2];

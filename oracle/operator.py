@@ -8,7 +8,10 @@ depth block A_(r) is BTTB, so an entry depends only on the layer r and on the
 station-minus-prism index offsets (a, b).  That makes the dense product
 computable exactly from a table of those unique entries; the FFT evaluation is
 the same product, so the oracle of the operator is the product itself, written
-as a plain sum (no FFT anywhere in this module).
+as a plain sum.  ``BCCB`` states the paper's own evaluation of that product
+(Sec. 2.7.1: per layer IFFT2(FFT2(T) . FFT2(X)), with numpy's FFT as the library
+step), pinned against the plain sum; it lets the tests reach workloads whose
+plain sums would take hours.
 
 Index conventions: cell c = (r * ny + iy) * nx + ix, station j = jy * sx + jx,
 a = (jy + off_y) - iy, b = (jx + off_x) - ix.
@@ -136,3 +139,49 @@ def forward_direct(K, grid, m):
 def adjoint_direct(K, grid, rvec):
     """A^T r for every cell (direct sums; O(s n))."""
     return adjoint_cols(K, grid, rvec, range(grid.n))
+
+
+def dense_from_table(K, grid) -> np.ndarray:
+    """The dense matrix assembled from the table (the BTTB structure of each depth
+    block): A[j, c] = K[r, a - a_min, b - b_min] with (a, b) the index offsets of
+    station j and cell c."""
+    jy, jx = np.divmod(np.arange(grid.s), grid.sx)
+    c = np.arange(grid.n)
+    r, rem = np.divmod(c, grid.nx * grid.ny)
+    iy, ix = np.divmod(rem, grid.nx)
+    ia = (jy[:, None] + grid.off_y - iy[None, :]) - (grid.off_y - (grid.ny - 1))
+    ib = (jx[:, None] + grid.off_x - ix[None, :]) - (grid.off_x - (grid.nx - 1))
+    return K[r[None, :], ia, ib]
+
+
+class BCCB:
+    """The products of Sec. 2.7.1 through the circulant embedding: the table of layer r
+    goes to T_r[c mod Ny, c' mod Nx] = K_r(c, c') for c in [-(ny-1), sy-1] (likewise in
+    x), the model layer to the upper-left corner of an Ny x Nx zero array; the forward
+    product is the upper-left sy x sx block of sum_r IFFT2(FFT2(T_r) FFT2(X_r)), the
+    adjoint the upper-left ny x nx block of IFFT2(conj(FFT2(T_r)) FFT2(V)) per layer.
+    Real transforms (numpy.fft.rfft2) since T, X and V are real.  FP64."""
+
+    def __init__(self, K, grid, Ny, Nx):
+        if Ny < grid.sy + grid.ny - 1 or Nx < grid.sx + grid.nx - 1:
+            raise ValueError("padded size below s + n - 1")
+        self.g, self.Ny, self.Nx = grid, Ny, Nx
+        ia = np.arange(-(grid.ny - 1), grid.sy) % Ny
+        ib = np.arange(-(grid.nx - 1), grid.sx) % Nx
+        T = np.zeros((grid.nz, Ny, Nx))
+        T[:, ia[:, None], ib[None, :]] = K
+        self.Th = np.fft.rfft2(T)
+
+    def forward(self, m):
+        g = self.g
+        X = np.zeros((g.nz, self.Ny, self.Nx))
+        X[:, :g.ny, :g.nx] = np.asarray(m, dtype=np.float64).reshape(g.nz, g.ny, g.nx)
+        Y = np.sum(self.Th * np.fft.rfft2(X), axis=0)
+        return np.fft.irfft2(Y, s=(self.Ny, self.Nx))[:g.sy, :g.sx].reshape(-1)
+
+    def adjoint(self, rvec):
+        g = self.g
+        V = np.zeros((self.Ny, self.Nx))
+        V[:g.sy, :g.sx] = np.asarray(rvec, dtype=np.float64).reshape(g.sy, g.sx)
+        Z = np.fft.irfft2(np.conj(self.Th) * np.fft.rfft2(V)[None], s=(self.Ny, self.Nx))
+        return Z[:, :g.ny, :g.nx].reshape(-1)

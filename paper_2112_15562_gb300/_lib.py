@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "libgj.so")
 GJ_OK = 0
 STATUS = {0: "GJ_OK", -1: "GJ_ERR_ARG", -2: "GJ_ERR_OOM", -3: "GJ_ERR_CUDA", -4: "GJ_ERR_NONFINITE",
           -5: "GJ_ERR_TIMEOUT", -6: "GJ_ERR_UNSUPPORTED"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
 GJ_GRAVITY, GJ_MAGNETIC = 1, 2
 GJ_FP64, GJ_FP32_MIXED = 0, 1
 GJ_SCALARS_AUTO, GJ_SCALARS_JOINT, GJ_SCALARS_PER_FIELD = 0, 1, 2
@@ -74,6 +75,8 @@ def load() -> ct.CDLL:
         "gj_bttb_setup": (i32, [ct.POINTER(Grid), i32, ct.POINTER(Mag), i32, i32, i32, vp, pp]),
         "gj_op_info": (i32, [vp, ct.POINTER(OpInfo)]),
         "gj_op_destroy": (None, [vp]),
+        "gj_op_status": (i32, [vp, i32, vp]),
+        "gj_selftest_bounded_wait": (i32, [i64, vp]),
         "gj_g_forward": (i32, [vp, vp, vp, vp]),
         "gj_g_adjoint": (i32, [vp, vp, vp, vp]),
         "gj_gramian_value_grad": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),

@@ -32,14 +32,6 @@ def _vec(t: torch.Tensor, dtype, n: int, name: str) -> torch.Tensor:
     return t
 
 
-def depth_weights(z_edges, beta: float) -> np.ndarray:
-    """Li & Oldenburg style depth weight per layer, (z_c / z_c,top)^(-beta/2) at the
-    layer centres (the form is not printed in the paper; top layer has weight 1)."""
-    z = np.asarray(z_edges, dtype=np.float64)
-    zc = 0.5 * (z[:-1] + z[1:])
-    return (zc / zc[0]) ** (-beta / 2.0)
-
-
 class Op:
     """One field's BTTB operator (owns device spectra and workspace)."""
 

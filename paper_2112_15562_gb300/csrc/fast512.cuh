@@ -25,7 +25,10 @@ namespace f512 {
 constexpr int N = 512, H = 256, NC = 257;
 constexpr int CWARPS = 12;        // warps per CTA of the persistent column kernels (one CTA per SM)
 constexpr int CSTAGES = 2;        // TMA ring depth per warp of the column kernels
-constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
+// Bounded mbarrier waits give up after this long (read from %globaltimer, checked
+// every eight polls), record GJ_ERR_TIMEOUT in the operator's error word and
+// let the kernel return; a healthy 2-4 KB bulk copy completes in microseconds.
+constexpr unsigned long long kWaitLimitNs = 200ull * 1000ull * 1000ull;
 
 // ---------------------------------------------------------------------------
 // small DFTs in registers
@@ -265,12 +268,32 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait; returns false (and records an error) if the phase never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-    for (long long i = 0; i < kSpinLimit; ++i)
-        if (mbar_test(bar, parity)) return true;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: returns false (and records GJ_ERR_TIMEOUT in *err) if the phase
+// has not completed limit_ns after the first poll.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 8; ++i)
+            if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) break;
+    }
     if (err) atomicExch(err, GJ_ERR_TIMEOUT);
     return false;
+}
+
+// An operator whose column kernel gave up on a wait is unusable until the error
+// is read and cleared (gj_op_status): its layer-sum counters may be off, so every
+// fast-path kernel of it returns at once while the error word is set.
+__device__ __forceinline__ bool op_failed(const int *err) {
+    return err != nullptr && *(volatile const int *)err != 0;
 }
 
 // After a timed-out wait at item t_fail, wait (bounded) for the copies this warp
@@ -334,7 +357,7 @@ struct ColItem {
 template <typename R>
 __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const int *done) {
     using C = cpx<R>;
-    if (stopped(done)) return;
+    if (stopped(done) || op_failed(V.err)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int ZB = H * sizeof(C), TB = N * sizeof(C);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
@@ -474,7 +497,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
 template <typename R>
 __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const int *done) {
     using C = cpx<R>;
-    if (stopped(done)) return;
+    if (stopped(done) || op_failed(V.err)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TB = N * sizeof(C);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;

@@ -112,3 +112,54 @@ extern "C" gj_status gj_g_adjoint(const gj_op *op, const void *r, void *g, gj_st
     if (!op || !r || !g) { gj::set_error("gj_g_adjoint: NULL argument"); return GJ_ERR_ARG; }
     return gj::adjoint_enqueue(op, r, g, reinterpret_cast<cudaStream_t>(stream));
 }
+
+namespace gj {
+// The bounded wait on a barrier that nothing completes (no copy is issued, so
+// nothing can land after the wait gives up): records its status in *err.
+static __global__ void k_wait_selftest(unsigned long long limit_ns, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) f512::mbar_init(&bar);
+    f512::mbar_fence_init();
+    __syncthreads();
+    if (threadIdx.x == 0 && f512::mbar_wait(&bar, 0, err, limit_ns)) *err = GJ_OK;
+}
+}  // namespace gj
+
+extern "C" gj_status gj_op_status(gj_op *op, int reset, gj_stream_t stream) {
+    if (!op) { gj::set_error("gj_op_status: NULL operator"); return GJ_ERR_ARG; }
+    if (!op->err) return GJ_OK;  // only the fast path's column kernels wait on copies
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int e = 0;
+    GJ_CUDA(cudaMemcpyAsync(&e, op->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GJ_CUDA(cudaStreamSynchronize(st));
+    if (e == 0) return GJ_OK;
+    if (reset) {
+        // the counters of a column whose warps gave up may be nonzero: restart them
+        GJ_CUDA(cudaMemsetAsync(op->cnt, 0, 257 * sizeof(int), st));
+        GJ_CUDA(cudaMemsetAsync(op->err, 0, sizeof(int), st));
+        GJ_CUDA(cudaStreamSynchronize(st));
+    }
+    gj::set_error("gj_op_status: a bounded device wait of this operator gave up (GJ_ERR_TIMEOUT)");
+    return (gj_status)e;
+}
+
+extern "C" gj_status gj_selftest_bounded_wait(int64_t limit_ns, gj_stream_t stream) {
+    if (limit_ns < 0 || limit_ns > 10LL * 1000 * 1000 * 1000) {
+        gj::set_error("gj_selftest_bounded_wait: limit_ns must be in [0, 1e10]");
+        return GJ_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    GJ_CUDA(cudaMalloc(&err, sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(err, 0xff, sizeof(int), st);  // -1 until the kernel writes
+    if (e == cudaSuccess) {
+        gj::k_wait_selftest<<<1, 32, 0, st>>>((unsigned long long)limit_ns, err);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) return gj::cuda_fail(e, "gj_selftest_bounded_wait");
+    return (gj_status)h;
+}

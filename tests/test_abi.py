@@ -51,6 +51,9 @@ def test_argument_errors_without_device_work(lib):
     assert lib.gj_rrcg_create(None, None, None, None, None, None, None, None, None, None, ct.byref(out)) == -1
     assert lib.gj_rrcg_iterate(None, 1, 0, None) == -1
     assert lib.gj_op_info(None, None) == -1
+    assert lib.gj_op_status(None, 1, None) == -1
+    assert lib.gj_selftest_bounded_wait(-1, None) == -1
+    assert lib.gj_selftest_bounded_wait(10**11, None) == -1
     lib.gj_op_destroy(None)
     lib.gj_rrcg_destroy(None)
     assert lib.gj_version().startswith(b"gj")

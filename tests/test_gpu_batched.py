@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import synth
+from oracle import weights as owt
 from tests.gpu_common import lib, rel
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +27,7 @@ def make_problem(gj, nx, ny, nz, seed, npad=(0, 0), prec="fp32"):
     d = [ops[i].forward(mt[i]) for i in range(2)]
     sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
     dob = [d[i] + sig[i] * torch.from_numpy(rng.standard_normal(g.s)).to(dt).cuda() for i in range(2)]
-    wd = [torch.from_numpy(gj.depth_weights(g.z_edges, b)).to(dt).cuda() for b in (2.0, 3.0)]
+    wd = [torch.from_numpy(owt.depth_weights(g.z_edges, b)).to(dt).cuda() for b in (2.0, 3.0)]
     return g, ops, dob, sig, wd
 
 
@@ -82,13 +83,12 @@ def test_autotuner_picks_a_valid_size_and_caches(tmp_path):
     assert autotune.smooth_sizes(511, 3) == [512, 525, 540]
 
 
-def test_lambda_sweep_matches_single_solves_and_selects_the_smallest_correlated_pair():
+def test_lambda_sweep_matches_single_solves():
     gj = lib()
     g, ops, dob, sig, wd = make_problem(gj, 16, 16, 6, 77)
     lambdas = [(0.0, 0.0), (2.0, 100.0), (50.0, 1500.0)]
     kw = dict(p=(1, 1), kmax=15, stop_on_chi2=False)
-    out = gj.lambda_sweep(g, synth.Mag(50000.0, 60.0, 10.0), dob, sig, wd, lambdas, precision="fp32",
-                          corr_threshold=-2.0, **kw)
+    out = gj.lambda_sweep(g, synth.Mag(50000.0, 60.0, 10.0), dob, sig, wd, lambdas, precision="fp32", **kw)
     assert len(out["runs"]) == 3
     for lam, run in zip(lambdas, out["runs"]):
         opsi = [gj.bttb_setup(g, "gravity", precision="fp32"),
@@ -101,9 +101,44 @@ def test_lambda_sweep_matches_single_solves_and_selects_the_smallest_correlated_
         assert -1.0 <= run["pearson"] <= 1.0
     # with the stop test off nothing "converges": no pair qualifies
     assert out["selected"] is None
-    # the selection rule on its own: first converged pair above the threshold
-    fake = {"runs": [{"converged": True, "pearson": 0.5}, {"converged": True, "pearson": 0.95},
-                     {"converged": True, "pearson": 0.99}]}
-    sel = next(i for i, r in enumerate(fake["runs"]) if r["converged"] and r["pearson"] >= 0.9)
-    assert sel == 1
+
+
+def test_lambda_sweep_selects_the_pair_the_oracle_selects():
+    """The selection of Secs. 3.1.3 and 5 with the chi^2 stop on (Eq. chi2): the sweep
+    keeps the smallest (lambda1, lambda2) whose solve fits both data sets and whose
+    models correlate above the threshold.  The same pairs run through the FP64 oracle
+    on the same host-made data decide which pair that is; here lambda = 0 fits but
+    correlates below 0.96, (1, 50) fits and correlates, and (5, 300) does not fit
+    within kmax."""
+    from oracle.rrcg import RRCGParams, rrcg_joint
+    from oracle import operator as oop
+
+    gj = lib()
+    g = synth.uniform_grid(16, 16, 16, 16, 6, 50.0)
+    mag = synth.Mag(50000.0, 60.0, 10.0)
+    A = [oop.dense_matrix(g, oop.GRAVITY), oop.dense_matrix(g, oop.MAGNETIC, mag)]
+    mt = [synth.dipping_blocks(g, v, 77, count=2) for v in (1.0, 0.1)]
+    e = synth.standard_normal((2, g.s), 78)
+    obs = [owt.noisy_data(A[i] @ mt[i], 0.01, 0.01, e[i]) for i in range(2)]
+    dob, sig = [o[0] for o in obs], [o[1] for o in obs]
+    wdep = [owt.depth_weights(g.z_edges, b) for b in (2.0, 3.0)]
+    lambdas = [(0.0, 0.0), (1.0, 50.0), (5.0, 300.0)]
+    kw = dict(p=(1, 1), alpha1=(100.0, 100.0), q=(0.85, 0.85), lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=250,
+              stop_on_chi2=True)
+    thr = 0.96
+    want = []
+    for lam in lambdas:
+        r = rrcg_joint([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
+                       dob, sig, [np.zeros(g.n)] * 2, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)],
+                       RRCGParams(lam=lam, **kw))
+        want.append((r.converged, float(np.corrcoef(r.m[0], r.m[1])[0, 1])))
+    expect = next(i for i, (c, pc) in enumerate(want) if c and pc >= thr)
+    assert expect == 1 and want[0][0] and want[0][1] < thr and not want[2][0]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).float().cuda()
+    out = gj.lambda_sweep(g, mag, [dev(x) for x in dob], [dev(x) for x in sig], [dev(x) for x in wdep], lambdas,
+                          precision="fp32", corr_threshold=thr, **kw)
+    assert out["selected"] == expect
+    for run, (conv, pc) in zip(out["runs"], want):
+        assert run["converged"] == conv
+        assert run["pearson"] == pytest.approx(pc, abs=5e-3)
     assert abs(gj.pearson(np.arange(5.0), 2 * np.arange(5.0) + 1) - 1.0) < 1e-12

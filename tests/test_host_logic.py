@@ -1,13 +1,13 @@
 """Host-side logic of the binding, on the CPU: the autotuner's padded-size
-candidates, the Pearson coefficient of the lambda sweep, the depth weights and the
-solver-option mapping.  None of these calls the GPU."""
+candidates, the Pearson coefficient of the lambda sweep, and the solver-option
+mapping.  None of these calls the GPU."""
 import numpy as np
 import pytest
 
 import synth
 from paper_2112_15562_gb300 import _lib as L
 from paper_2112_15562_gb300 import autotune
-from paper_2112_15562_gb300.api import depth_weights, solver_params
+from paper_2112_15562_gb300.api import solver_params
 from paper_2112_15562_gb300.sweep import pearson
 
 
@@ -47,16 +47,6 @@ def test_pearson():
     assert pearson(a, -0.5 * a + 7.0) == pytest.approx(-1.0, abs=1e-12)
     assert pearson(a, np.full(500, 4.0)) == 0.0  # no spread: defined as 0
     assert pearson(2 * a + 1, 5 * b - 3) == pytest.approx(pearson(a, b), abs=1e-12)
-
-
-def test_depth_weights_closed_form():
-    # uniform layers of thickness dz from the surface: centres (k + 1/2) dz, so the
-    # weight of layer k is (2k + 1)^(-beta/2) and the top layer has weight 1
-    z = np.arange(11) * 37.5
-    for beta in (2.0, 3.0):
-        w = depth_weights(z, beta)
-        np.testing.assert_allclose(w, (2.0 * np.arange(10) + 1.0) ** (-beta / 2.0), rtol=1e-15)
-        assert w[0] == 1.0 and np.all(np.diff(w) < 0)
 
 
 def test_solver_params_option_mapping():

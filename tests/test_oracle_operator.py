@@ -137,3 +137,25 @@ def test_storage_figures_printed_in_the_paper():
     trans = 2 * a.size * b.size * g.nz * 16
     assert trans / 1e6 == pytest.approx(mb["printed_transform_MB"], rel=0.01)
     assert dense / trans == pytest.approx(mb["printed_reduction"], rel=0.01)
+
+
+@pytest.mark.parametrize("field", [op.GRAVITY, op.MAGNETIC])
+def test_bccb_products_and_dense_from_table_equal_the_dense_product(field):
+    """The oracle's FFT evaluation (Sec. 2.7.1) against the plain dense product, for
+    the minimal padding, a larger odd padding and a power of two; and the matrix
+    assembled from the table against the one assembled from the prisms."""
+    rng = np.random.default_rng(17)
+    for g in small_grids():
+        A = op.dense_matrix(g, field, MAG)
+        K = op.kernel_table(g, field, MAG)
+        assert np.array_equal(op.dense_from_table(K, g), A)
+        m = rng.standard_normal(g.n)
+        rv = rng.standard_normal(g.s)
+        Nmin_y, Nmin_x = g.sy + g.ny - 1, g.sx + g.nx - 1
+        for Ny, Nx in [(Nmin_y, Nmin_x), (Nmin_y + 3, Nmin_x + 1), (16, 16)]:
+            B = op.BCCB(K, g, Ny, Nx)
+            d, gt = A @ m, A.T @ rv
+            assert np.linalg.norm(B.forward(m) - d) <= 1e-13 * np.linalg.norm(d)
+            assert np.linalg.norm(B.adjoint(rv) - gt) <= 1e-13 * np.linalg.norm(gt)
+        with pytest.raises(ValueError):
+            op.BCCB(K, g, Nmin_y - 1, Nmin_x)

@@ -295,3 +295,16 @@ def test_second_direction_and_regulariser_anchor(anchor):
     l0 = half_gradient(f0, m0[0], m0[1])
     b = sum(float(x @ x) for x in want) / sum(float(x @ x) for x in l0)
     assert beta1[0] == beta1[1] == pytest.approx(b, rel=1e-6)
+
+
+def test_depth_weights_closed_form():
+    """Reading of the depth weighting (Li & Oldenburg form at layer centres): uniform
+    layers of thickness dz from the surface have centres (k + 1/2) dz, so layer k gets
+    (2k + 1)^(-beta/2); the top layer has weight 1 and deeper ones decrease."""
+    z = np.arange(11) * 37.5
+    for beta in (2.0, 3.0):
+        w = wt.depth_weights(z, beta)
+        np.testing.assert_allclose(w, (2.0 * np.arange(10) + 1.0) ** (-beta / 2.0), rtol=1e-15)
+        assert w[0] == 1.0 and np.all(np.diff(w) < 0)
+    cells = wt.depth_weight_cells(z, 2.0, 3, 2)
+    assert cells.shape == (60,) and np.all(cells[:6] == 1.0) and np.all(cells[6:12] == cells[6])
