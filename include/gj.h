@@ -256,6 +256,22 @@ gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrcg_params *p
                               const void *const w_hard[2], void *const m[2],
                               gj_rrcg_hist *hist, gj_rrcg_report *rep, gj_stream_t stream);
 
+/*
+ * gj_rrcg_joint_solve_host - the same solve with HOST buffers: dobs, sigma,
+ * w_depth, m_apr, w_hard and m are host pointers (m: the starting models on
+ * entry, the result on return); everything else is as in gj_rrcg_joint_solve
+ * (no history).  The call allocates one device block for the copies, copies
+ * the inputs in with cudaMemcpyAsync on `stream` (page-locked host memory lets
+ * the copies run asynchronously), solves, copies both models back, frees the
+ * block and synchronises `stream`.  On GJ_ERR_NONFINITE the models are still
+ * copied back.
+ */
+gj_status gj_rrcg_joint_solve_host(const gj_op *const ops[2], const gj_rrcg_params *params,
+                                   const void *const dobs[2], const void *const sigma[2],
+                                   const void *const m_apr[2], const void *const w_depth[2],
+                                   const void *const w_hard[2], void *const m[2],
+                                   gj_rrcg_report *rep, gj_stream_t stream);
+
 /* Stepwise form of the same solve: a solver object holds the state (search
  * directions, scalars) and enqueues whole iterations without host round trips;
  * the stop test runs on the device and later iterations become no-ops. */
@@ -300,6 +316,17 @@ typedef struct gj_rrcg_batch gj_rrcg_batch;
 gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj_stream_t stream, gj_rrcg_batch **out);
 gj_status gj_rrcg_batch_step(gj_rrcg_batch *batch, int iters, gj_stream_t stream);
 void gj_rrcg_batch_destroy(gj_rrcg_batch *batch);
+
+/*
+ * gj_probe_fma_rate - measures the device's fused multiply-add rate (a roofline
+ * denominator for the FFT kernels; the paper has no counterpart).  kind 0: FP32
+ * fma.rn.f32, 1: paired FP32 fma.rn.f32x2 (two FMAs per instruction), 2: FP64
+ * fma.rn.f64.  A grid of 8 blocks of 256 threads per SM runs `iters` x 128
+ * independent FMAs per thread (eight chains); the second of two launches is
+ * timed with CUDA events on `stream`.  *gflops = 2 x FMAs / time, *ms = the
+ * launch's time.  Synchronous; allocates 8 bytes of device memory.
+ */
+gj_status gj_probe_fma_rate(int kind, int iters, double *gflops, double *ms, gj_stream_t stream);
 
 /* Last error message of the calling thread ("" if none). */
 const char *gj_last_error(void);

@@ -83,6 +83,8 @@ def load() -> ct.CDLL:
         "gj_gramian_value_grad_noalloc": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),
         "gj_rrcg_joint_solve": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp, vp,
                                       ct.POINTER(RRCGReport), vp]),
+        "gj_rrcg_joint_solve_host": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp,
+                                           ct.POINTER(RRCGReport), vp]),
         "gj_rrcg_create": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp, vp, vp, pp]),
         "gj_rrcg_iterate": (i32, [vp, i32, i32, vp]),
         "gj_rrcg_report_get": (i32, [vp, ct.POINTER(RRCGReport), vp]),
@@ -93,6 +95,7 @@ def load() -> ct.CDLL:
         "gj_rrcg_batch_create": (i32, [pp, i32, vp, pp]),
         "gj_rrcg_batch_step": (i32, [vp, i32, vp]),
         "gj_rrcg_batch_destroy": (None, [vp]),
+        "gj_probe_fma_rate": (i32, [i32, i32, ct.POINTER(d), ct.POINTER(d), vp]),
         "gj_last_error": (ct.c_char_p, []),
         "gj_version": (ct.c_char_p, []),
     }

@@ -247,22 +247,54 @@ def rrcg_joint_solve(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_dep
     return out
 
 
-def rrcg_joint_solve_host(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_depth, m0, stream=None):
-    """The same solve with host (numpy) inputs: copies in, solves, copies the models out.
-    Returns (models as numpy arrays, report, bytes copied in, bytes copied out)."""
-    dt = ops[0].dtype
-    dev = torch.device("cuda")
-    pin = [torch.from_numpy(np.ascontiguousarray(x)).to(dt).pin_memory()
-           for x in list(dobs) + list(sigma) + list(w_depth) + list(m0)]
-    dv = [t.to(dev, non_blocking=True) for t in pin]
-    rep = rrcg_joint_solve(ops, params, dv[0:2], dv[2:4], dv[4:6], dv[6:8], stream=stream)
-    out = [torch.empty(t.shape, dtype=dt).pin_memory() for t in dv[6:8]]
-    for o_, t in zip(out, dv[6:8]):
-        o_.copy_(t, non_blocking=True)
-    torch.cuda.current_stream().synchronize()
-    bin_ = sum(t.numel() * t.element_size() for t in pin)
-    bout = sum(t.numel() * t.element_size() for t in out)
-    return [o_.numpy() for o_ in out], rep, bin_, bout
+def _host_vec(x, dtype, n: int, name: str, writable: bool = False):
+    """A host buffer for the C ABI: a contiguous CPU tensor (e.g. page-locked) or numpy
+    array of the op's dtype and length n; returns (keep-alive object, address)."""
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or x.dtype != dtype or not x.is_contiguous() or x.numel() != n:
+            raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor of {n} values")
+        return x, x.data_ptr()
+    a = np.asarray(x)
+    want = np.float64 if dtype == torch.float64 else np.float32
+    if a.dtype != want or not a.flags.c_contiguous or a.size != n or (writable and not a.flags.writeable):
+        raise ValueError(f"{name} must be a contiguous writable {want.__name__} array of {n} values")
+    return a, a.ctypes.data
+
+
+def rrcg_joint_solve_host(ops: Sequence[Op], params: L.RRCGParams, dobs, sigma, w_depth, m, m_apr=None,
+                          w_hard=None, stream=None) -> dict:
+    """gj_rrcg_joint_solve_host: the solve with host buffers (CPU tensors or numpy arrays of
+    the op's dtype); the library copies them in, solves and copies the models back into m.
+    The report carries the bytes copied each way."""
+    o = ops[0]
+    keep = []
+
+    def arr(vals, name, n, allow_none=False, writable=False):
+        if vals is None:
+            return None
+        a = (ct.c_void_p * 2)()
+        for i in range(2):
+            if vals[i] is None:
+                if not allow_none:
+                    raise ValueError(f"{name}[{i}] is required")
+                a[i] = None
+            else:
+                k, ptr = _host_vec(vals[i], o.dtype, n, f"{name}[{i}]", writable)
+                keep.append(k)
+                a[i] = ptr
+        return a
+
+    handles = (ct.c_void_p * 2)(ops[0].handle.value, ops[1].handle.value)
+    rep = L.RRCGReport()
+    args = (arr(dobs, "dobs", o.s), arr(sigma, "sigma", o.s), arr(m_apr, "m_apr", o.n, True),
+            arr(w_depth, "w_depth", o.info.nz), arr(w_hard, "w_hard", o.n, True), arr(m, "m", o.n, writable=True))
+    check(load().gj_rrcg_joint_solve_host(handles, ct.byref(params), *args, ct.byref(rep), _stream(stream)))
+    es = 8 if o.dtype == torch.float64 else 4
+    out = _report(rep)
+    nin = 2 * (2 * o.s + o.info.nz + o.n) + (2 * o.n if m_apr is not None else 0) + (2 * o.n if w_hard is not None else 0)
+    out["h2d_bytes"] = nin * es
+    out["d2h_bytes"] = 2 * o.n * es
+    return out
 
 
 class Batch:

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build", "gj")
 LIB = os.path.join(HERE, "libgj.so")
-SOURCES = ["api.cu", "setup.cu", "matvec.cu", "gramian.cu", "rrcg.cu"]
+SOURCES = ["api.cu", "setup.cu", "matvec.cu", "gramian.cu", "rrcg.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

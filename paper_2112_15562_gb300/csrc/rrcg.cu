@@ -1250,3 +1250,72 @@ extern "C" void gj_rrcg_batch_destroy(gj_rrcg_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     delete b;
 }
+
+// ---------------------------------------------------------------------------
+// Host-buffer form of the one-shot solve: the inputs are copied to the device,
+// the solve runs as in gj_rrcg_joint_solve, and the models are copied back.
+
+extern "C" gj_status gj_rrcg_joint_solve_host(const gj_op *const ops[2], const gj_rrcg_params *P,
+                                              const void *const dobs[2], const void *const sigma[2],
+                                              const void *const m_apr[2], const void *const w_depth[2],
+                                              const void *const w_hard[2], void *const m[2], gj_rrcg_report *rep,
+                                              gj_stream_t stream) {
+    gj_status rc = check_ops(ops);
+    if (rc != GJ_OK) return rc;
+    if (!P || !dobs || !sigma || !w_depth || !m || !rep) {
+        set_error("gj_rrcg_joint_solve_host: NULL argument");
+        return GJ_ERR_ARG;
+    }
+    for (int i = 0; i < 2; ++i)
+        if (!dobs[i] || !sigma[i] || !w_depth[i] || !m[i]) {
+            set_error("gj_rrcg_joint_solve_host: NULL vector");
+            return GJ_ERR_ARG;
+        }
+    const gj_op *o = ops[0];
+    const size_t es = elem_bytes(o->prec);
+    const size_t n = (size_t)o->nx * o->ny * o->nz, s = (size_t)o->sx * o->sy, nz = (size_t)o->nz;
+    // one device block: dobs, sigma (s each), w_depth (nz), m, m_apr, w_hard (n each), per field
+    size_t per = 2 * s + nz + n;
+    if (m_apr && (m_apr[0] || m_apr[1])) per += n;
+    if (w_hard && (w_hard[0] || w_hard[1])) per += n;
+    char *blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, 2 * per * es);
+    if (e != cudaSuccess) return cuda_fail(e, "gj_rrcg_joint_solve_host: device buffers");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const void *d_dobs[2], *d_sig[2], *d_wdep[2], *d_mapr[2] = {nullptr, nullptr}, *d_wh[2] = {nullptr, nullptr};
+    void *d_m[2];
+    char *at = blk;
+    auto put = [&](const void *src, size_t count) -> const void * {
+        void *dst = at;
+        at += count * es;
+        if (src && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, count * es, cudaMemcpyHostToDevice, st);
+        return dst;
+    };
+    for (int i = 0; i < 2; ++i) {
+        d_dobs[i] = put(dobs[i], s);
+        d_sig[i] = put(sigma[i], s);
+        d_wdep[i] = put(w_depth[i], nz);
+        d_m[i] = const_cast<void *>(put(m[i], n));
+        if (m_apr && (m_apr[0] || m_apr[1])) {
+            const void *p = put(m_apr[i], n);
+            d_mapr[i] = m_apr[i] ? p : nullptr;
+        }
+        if (w_hard && (w_hard[0] || w_hard[1])) {
+            const void *p = put(w_hard[i], n);
+            d_wh[i] = w_hard[i] ? p : nullptr;
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaFree(blk);
+        return cuda_fail(e, "gj_rrcg_joint_solve_host: copies in");
+    }
+    rc = gj_rrcg_joint_solve(ops, P, d_dobs, d_sig, d_mapr, d_wdep, d_wh, d_m, nullptr, rep, stream);
+    if (rc == GJ_OK || rc == GJ_ERR_NONFINITE) {
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(m[i], d_m[i], n * es, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "gj_rrcg_joint_solve_host: copies out");
+    }
+    cudaFree(blk);
+    return rc;
+}

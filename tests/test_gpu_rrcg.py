@@ -223,3 +223,24 @@ def test_fast_solver_partial_line_groups(ragged, optional):
             assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-4), (k, i)
     for i in range(2):
         assert rel(m[i], ref.m[i]) <= 1e-4, (i, rel(m[i], ref.m[i]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_host_buffer_solve_matches_oracle(small, prec):
+    """gj_rrcg_joint_solve_host: numpy inputs, the library copies in and out."""
+    gj = lib()
+    w, g, A, dob, sig, wdep = small
+    kw = dict(KW, kmax=15)
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw))
+    npad = (0, 0) if prec == "fp64" else (512, 512)
+    ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
+           gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
+    nd = np.float64 if prec == "fp64" else np.float32
+    host = lambda xs: [np.ascontiguousarray(x, dtype=nd) for x in xs]
+    m = host([np.zeros(g.n), np.zeros(g.n)])
+    rep = gj.rrcg_joint_solve_host(ops, gj.solver_params(**kw), host(dob), host(sig), host(wdep), m)
+    assert rep["iterations"] == 15 and rep["status"] == 0
+    assert rep["h2d_bytes"] == (2 * (2 * g.s + g.nz + g.n)) * nd().itemsize
+    tol = 1e-9 if prec == "fp64" else 1e-3
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= tol, (i, rel(m[i], ref.m[i]))
