@@ -46,11 +46,28 @@ def parse():
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, on a bounded sample
 
-def oracle_sample(grid_full, mag, rows: int, cols: int, layers: int = 4, seed: int = 0):
-    """Times the oracle's direct sums on a sample and extrapolates to one RRCG
-    iteration (2 forward products and 1 adjoint product per field).  Forward rows
-    are timed on the top ``layers`` layers and scaled by nz / layers (the cost of
-    a row is linear in the layer count); adjoint cells are independent of nz."""
+def _rows_worker(args):
+    """Direct sums of the oracle for a chunk of forward rows and adjoint cells (one
+    process of the pool); returns the seconds it took."""
+    from oracle import operator as oop
+
+    K, grid, m, r, stations, cells = args
+    t0 = time.perf_counter()
+    oop.forward_rows(K, grid, m, stations)
+    oop.adjoint_cols(K, grid, r, cells)
+    return time.perf_counter() - t0
+
+
+def oracle_direct_all_cores(grid_full, mag, rows: int = 96, cols: int = 1536, layers: int = 4, seed: int = 0):
+    """The oracle's direct sums (the plain definition of the products) on a pool of
+    spawned processes, one per host core: ``rows`` forward rows over the top
+    ``layers`` layers (scaled to nz; a row's cost is linear in the layer count) and
+    ``cols`` adjoint cells per field, extrapolated to one RRCG iteration (2 forward
+    and 1 adjoint products per field).  Returns (iters/s, seconds per iteration,
+    processes, wall seconds)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
     import numpy as np
     import synth
     from oracle import operator as oop
@@ -58,24 +75,86 @@ def oracle_sample(grid_full, mag, rows: int, cols: int, layers: int = 4, seed: i
     g = grid_full
     sub = synth.uniform_grid(g.sx, g.sy, g.nx, g.ny, layers, g.dx)
     sub.z_edges = g.z_edges[:layers + 1].copy()
+    procs = os.cpu_count() or 1
     rng = np.random.default_rng(seed)
-    t_rows = t_cols = 0.0
-    for f in (oop.GRAVITY, oop.MAGNETIC):
-        K = oop.kernel_table(sub, f, mag)
-        m = rng.uniform(0, 1, sub.n)
-        r = rng.standard_normal(sub.s)
-        st = rng.integers(0, sub.s, rows)
-        cl = rng.integers(0, sub.n, cols)
-        t0 = time.perf_counter()
-        oop.forward_rows(K, sub, m, st)
-        t1 = time.perf_counter()
-        oop.adjoint_cols(K, sub, r, cl)
-        t2 = time.perf_counter()
-        t_rows += (t1 - t0) / rows * (g.nz / layers)
-        t_cols += (t2 - t1) / cols
-    # per field: 2 forward products (s rows) + 1 adjoint (n cells); t_* already sum both fields
-    per_iter = 2 * g.s * t_rows + g.n * t_cols
-    return 1.0 / per_iter, per_iter
+    jobs_rows, per_row, per_col = [], 0.0, 0.0
+    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(int, range(procs)))  # start the workers before timing
+        wall = 0.0
+        for f in (oop.GRAVITY, oop.MAGNETIC):
+            K = oop.kernel_table(sub, f, mag)
+            m = rng.uniform(0, 1, sub.n)
+            r = rng.standard_normal(sub.s)
+            st = np.array_split(rng.integers(0, sub.s, rows), procs)
+            cl = np.array_split(rng.integers(0, sub.n, cols), procs)
+            t0 = time.perf_counter()
+            list(ex.map(_rows_worker, [(K, sub, m, r, st[k], np.array([], dtype=int)) for k in range(procs)]))
+            t1 = time.perf_counter()
+            list(ex.map(_rows_worker, [(K, sub, m, r, np.array([], dtype=int), cl[k]) for k in range(procs)]))
+            t2 = time.perf_counter()
+            per_row += (t1 - t0) / rows * (g.nz / layers)
+            per_col += (t2 - t1) / cols
+            wall += t2 - t0
+    per_iter = 2 * g.s * per_row + g.n * per_col
+    return 1.0 / per_iter, per_iter, procs, wall
+
+
+def oracle_fft_iterations(w, iters: int, time_cap_s: float = 1e9, warmup: int = 0):
+    """Whole RRCG iterations of the oracle at the full workload, with its FFT evaluation
+    of the products (oracle.operator.BCCB, numpy FP64 on one core) and the same
+    solver settings as the GPU leg; the tables are built first and not timed.
+    Returns (seconds of each timed iteration, table seconds)."""
+    import numpy as np
+    from oracle import operator as oop
+    from oracle import weights as owt
+    from oracle.rrcg import RRCGParams, rrcg_joint
+
+    g = w.grid
+    t0 = time.perf_counter()
+    B = [oop.BCCB(oop.kernel_table(g, oop.GRAVITY), g, 512, 512),
+         oop.BCCB(oop.kernel_table(g, oop.MAGNETIC, w.mag), g, 512, 512)]
+    t_tab = time.perf_counter() - t0
+    obs = [owt.noisy_data(B[i].forward(w.m_true[i]), 0.01, 0.01, w.noise[i]) for i in range(2)]
+    dob, sig = [o[0] for o in obs], [o[1] for o in obs]
+    wst = [owt.depth_weight_cells(g.z_edges, b, g.nx, g.ny) for b in (2.0, 3.0)]
+    stamps = []
+
+    def fwd(i):
+        def f(x):
+            if i == 0:
+                stamps.append(time.perf_counter())
+            return B[i].forward(x)
+        return f
+
+    # one solve of kmax iterations; the forward of the gravity model opens each
+    # iteration's timed span (the first, the residual of m_0, is setup)
+    kmax = warmup + iters
+    P = RRCGParams(p=(1, 1), alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(5.0, 20.0), lam=(2.0, 100.0),
+                   lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=kmax, stop_on_chi2=False)
+    t_start = time.perf_counter()
+
+    class Capped(Exception):
+        pass
+
+    def fwd_capped(i):
+        inner = fwd(i)
+
+        def f(x):
+            if i == 0 and time.perf_counter() - t_start > time_cap_s:
+                raise Capped()
+            return inner(x)
+        return f
+
+    try:
+        rrcg_joint([fwd_capped(0), fwd_capped(1)], [B[0].adjoint, B[1].adjoint], dob, sig,
+                   [np.zeros(g.n)] * 2, wst, P)
+    except Capped:
+        pass
+    # gravity forwards per iteration: the residual of m_k and the product of p_k, so an
+    # iteration spans two stamps
+    starts = stamps[0::2]
+    spans = [b - a for a, b in zip(starts[:-1], starts[1:])]
+    return spans[warmup:], t_tab
 
 
 def run_reference(args, rank):
@@ -84,21 +163,17 @@ def run_reference(args, rank):
     if rank != 0:
         return
     w = synth.joint_256()
-    vals = []
     t0 = time.perf_counter()
-    for k in range(args.warmup + args.steps):
-        v, _ = oracle_sample(w.grid, w.mag, rows=8, cols=64, seed=k)
-        if k >= args.warmup:
-            vals.append(v)
+    spans, t_tab = oracle_fft_iterations(w, args.steps, time_cap_s=240.0, warmup=args.warmup)
     wall = time.perf_counter() - t0
-    val = statistics.median(vals)
+    val = 1.0 / statistics.median(spans)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
+            "steps": len(spans), "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: 8 forward rows (top 4 layers, scaled to 40) and 64 adjoint cells "
-                                       "per field by direct sums, extrapolated to 2 forward + 1 adjoint products "
-                                       f"per field; wall {wall:.1f} s"},
+                             "sample": f"{len(spans)} whole RRCG iterations at 256x256x40 (of {args.steps} asked; "
+                                       "240 s cap) by the oracle with its numpy-FFT FP64 evaluation of the products "
+                                       f"(one core); tables {t_tab:.1f} s untimed; wall {wall:.1f} s"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -303,17 +378,29 @@ def run_ours(args, rank, world, local_rank):
         line["config"]["parallelism"] = f"replicas x{world} (independent inversions, no collective)"
 
     if not args.no_extras and rank == 0:
+        line["alu_peaks"] = alu_leg(gj, torch)
+        line["roofline"]["alu"] = alu_fraction(o, avg_ms, line["alu_peaks"])
         line["operator"] = operator_leg(torch, ops, g, dev, flush, hbm)
-        line["fp64"] = fp64_leg(gj, torch, dev, flush, value)
+        line["fp64"] = fp64_leg(gj, torch, dev, flush, value, hbm, line["alu_peaks"])
+        line["p2"] = p2_leg(gj, torch, ops, g, dobs, sigma, wdep, dev, flush)
+        line["operator_128"] = c2_leg(gj, torch, dev, flush, hbm)
         line["e2e"] = e2e_leg(gj, torch, ops, g, dobs, sigma, wdep)
         line["batched"] = batched_leg(gj, torch, dev, flush)
         line["paper_shapes"] = paper_shapes_leg(gj, torch, dev, flush)
         if world == 1:
-            v, per = oracle_sample(w.grid, w.mag, rows=24, cols=400)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "24 forward rows (top 4 layers, scaled to 40) and 400 adjoint cells per "
-                                              "field by direct sums, extrapolated to one iteration "
-                                              f"({per:.0f} s per iteration)"}
+            spans, t_tab = oracle_fft_iterations(w, 2)
+            v_all, per_all, procs, wall_all = oracle_direct_all_cores(w.grid, w.mag)
+            c1 = oracle_c1_solve()
+            line["cpu_baseline"] = {
+                "value": 1.0 / statistics.median(spans), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"2 whole RRCG iterations at 256x256x40 by the oracle with its numpy-FFT FP64 evaluation "
+                          f"of the products, one core (tables {t_tab:.1f} s, untimed)",
+                "direct_sums_all_cores": {"value": v_all, "unit": UNIT, "cores": procs,
+                                          "seconds_per_iteration": per_all, "wall_s": wall_all,
+                                          "sample": "96 forward rows (top 4 layers, scaled to 40) and 1536 adjoint "
+                                                    "cells per field by the oracle's direct sums on a spawned pool "
+                                                    "of one process per core, extrapolated to one iteration"},
+                "c1_dense_rrcg": c1}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -343,19 +430,22 @@ def profiled_traffic(fast):
     return (float(m_rd.group(1)) + float(m_wr.group(1))) * 1e6, "profiles/k_col_fwd512_joint256.md (ncu, cold L2)"
 
 
-def operator_leg(torch, ops, g, dev, flush, hbm, steps=50):
-    """G m + G^T r for both fields through gj_g_forward / gj_g_adjoint (FP32)."""
-    m = [torch.rand(g.n, device=dev) for _ in range(2)]
-    r = [torch.randn(g.s, device=dev) for _ in range(2)]
-    d = [torch.empty(g.s, device=dev) for _ in range(2)]
-    a = [torch.empty(g.n, device=dev) for _ in range(2)]
+def operator_leg(torch, ops, g, dev, flush, hbm, steps=50, elem=4):
+    """G m + G^T r for both fields through gj_g_forward / gj_g_adjoint, in the ops'
+    precision (elem bytes per real).  flush=None times warm (no L2 flush)."""
+    dt = ops[0].dtype
+    m = [torch.rand(g.n, device=dev, dtype=dt) for _ in range(2)]
+    r = [torch.randn(g.s, device=dev, dtype=dt) for _ in range(2)]
+    d = [torch.empty(g.s, device=dev, dtype=dt) for _ in range(2)]
+    a = [torch.empty(g.n, device=dev, dtype=dt) for _ in range(2)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     res = {}
     for name in ("forward", "adjoint"):
         ts = []
-        for k in range(steps + 5):
-            flush.fill_(float(k))
+        for k in range(steps + 3):
+            if flush is not None:
+                flush.fill_(float(k))
             e0.record()
             for i in range(2):
                 if name == "forward":
@@ -364,29 +454,162 @@ def operator_leg(torch, ops, g, dev, flush, hbm, steps=50):
                     ops[i].adjoint(r[i], a[i])
             e1.record()
             e1.synchronize()
-            if k >= 5:
+            if k >= 3:
                 ts.append(e0.elapsed_time(e1))
         res[name] = statistics.median(ts)
     o = ops[0].info
-    S_mag = o.nz * o.Ny * o.ncol * 8
-    per_pair = 2 * (4 * g.n + 4 * g.s) + S_mag + S_mag // 2
+    S_mag = o.nz * o.Ny * o.ncol * 2 * elem
+    # per product: model and data vectors plus the layer spectra (the gravity table is
+    # even in both offsets, so its spectrum is real: half the bytes)
+    per_pair = 2 * (elem * g.n + elem * g.s) + S_mag + S_mag // 2
     tot = res["forward"] + res["adjoint"]
     gbs = 2 * per_pair / (tot * 1e-3) / 1e9
     return {"forward_pair_ms": res["forward"], "adjoint_pair_ms": res["adjoint"],
             "algorithmic_bytes_fwd_plus_adj": 2 * per_pair, "algorithmic_GBs": gbs, "frac_of_hbm": gbs / hbm,
-            "note": "both fields, standalone C-ABI calls, L2 flushed, medians of 50"}
+            "note": f"both fields, standalone C-ABI calls, {'L2 flushed' if flush is not None else 'warm'}, "
+                    f"medians of {steps}"}
 
 
-def fp64_leg(gj, torch, dev, flush, v32, steps=8, warmup=2):
+def fp64_leg(gj, torch, dev, flush, v32, hbm, alu, steps=8, warmup=2):
+    """The plain FP64 form (every vector, spectrum and FFT in FP64, generic kernels):
+    the RRCG iteration and the standalone G m + G^T r of both fields."""
     w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp64", dev)
     sv, m, P = solver_for(gj, torch, ops, g, dobs, sigma, wdep, steps + warmup + 2, dev)
     times, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
     sv.close()
+    ms = sum(times) / steps
+    opl = operator_leg(torch, ops, g, dev, flush, hbm, steps=10, elem=8)
     for o in ops:
         o.close()
+    out = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "fp32_speedup": v32 / (1e3 / ms), "dtype": "f64 (plain FP64 form)", "operator": opl}
+    # FFT flops of one iteration (5 N log2 N per complex 512-point transform, the
+    # transforms of the generic kernels: row and column passes of 6 products)
+    fl = iteration_fft_flops(g)
+    out["fft_GFLOPs_per_iteration"] = fl / 1e9
+    if alu and alu.get("fp64_fma_tflops"):
+        out["frac_of_fp64_fma_peak"] = fl / (ms * 1e-3) / 1e12 / alu["fp64_fma_tflops"]
+    return out
+
+
+def iteration_fft_flops(g, N=512):
+    """5 N log2 N flops per complex N-point transform (the usual FFT count) over the
+    transforms of one RRCG iteration on an N x N embedding: per field 2 forward
+    products (rows: ny nz real lines, two per complex transform; columns: (N/2 + 1) nz
+    transforms; one inverse column transform per column; sy/2 inverse row transforms)
+    and 1 adjoint product (the reverse)."""
+    import math
+
+    f = 5 * N * math.log2(N)
+    per_product = (g.ny * g.nz / 2 + (N // 2 + 1) * g.nz + (N // 2 + 1) + g.sy / 2) * f
+    return 2 * 3 * per_product
+
+
+def alu_leg(gj, torch):
+    """FMA rates of the device (gj_probe_fma_rate), the compute roofline of the FFTs."""
+    import ctypes as ct
+
+    from paper_2112_15562_gb300 import _lib
+
+    L = _lib.load()
+    st = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    for kind, key, iters in ((0, "fp32_fma_tflops", 4000), (1, "fp32x2_fma_tflops", 4000), (2, "fp64_fma_tflops", 500)):
+        best = 0.0
+        for _ in range(3):
+            gf, ms = ct.c_double(), ct.c_double()
+            _lib.check(L.gj_probe_fma_rate(kind, iters, ct.byref(gf), ct.byref(ms), st))
+            best = max(best, gf.value / 1e3)
+        out[key] = best
+    out["note"] = ("gj_probe_fma_rate: 8 blocks of 256 threads per SM, 8 independent FMA chains per thread, "
+                   "best of 3 launches timed with CUDA events at the clocks of the moment; 2 flops per FMA")
+    return out
+
+
+def alu_fraction(o, avg_ms, alu):
+    """FFT flops of one launch of the dominant column kernel against the FP32 FMA rate:
+    per field and layer (N/2 + 1) forward 512-point transforms and the spectrum
+    multiply-adds, plus one inverse transform per column."""
+    import math
+
+    if not avg_ms or not alu.get("fp32_fma_tflops"):
+        return None
+    f = 5 * 512 * math.log2(512)
+    cols = o.ncol
+    fl = 2 * cols * o.nz * f + cols * o.nz * 512 * (8 + 4) + 2 * cols * f
+    ach = fl / (avg_ms * 1e-3) / 1e12
+    return {"flops_per_launch": fl, "achieved_tflops": ach, "fp32_fma_tflops": alu["fp32_fma_tflops"],
+            "frac": ach / alu["fp32_fma_tflops"],
+            "convention": "5 N log2 N per complex N-point transform; 8 (magnetic) and 4 (gravity, real spectrum) "
+                          "flops per spectrum multiply-add"}
+
+
+def p2_leg(gj, torch, ops, g, dobs, sigma, wdep, dev, flush, steps=20, warmup=3):
+    """The same workload with the minimum-length stabiliser (p = 2, Sec. 3.1.5)."""
+    m = [torch.zeros(g.n, dtype=ops[0].dtype, device=dev) for _ in range(2)]
+    P = gj.solver_params(p=(2, 2), lam=(2.0, 100.0), alpha1=(2e4, 2e4), q=(0.95, 0.95), alpha_min=(5.0, 20.0),
+                         lo=(0.0, 0.0), hi=(1.0, 0.1), kmax=steps + warmup + 2, stop_on_chi2=False)
+    sv = gj.Solver(ops, P, dobs, sigma, wdep, m)
+    times, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
+    sv.close()
     ms = sum(times) / steps
-    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "fp32_speedup": v32 / (1e3 / ms), "dtype": "f64 (plain FP64 form)"}
+    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps, "p": [2, 2]}
+
+
+def c2_leg(gj, torch, dev, flush, hbm, steps=20):
+    """128x128 stations over 128x128x32 cells: G m + G^T r of both fields at the padded
+    size 255 x 255 (3 x 5 x 17) and at the autotuned size, FP32 and FP64, with the L2
+    flushed before every repetition (cold) and without (warm, the operator fits in L2)."""
+    import tempfile
+
+    import synth
+    from paper_2112_15562_gb300 import autotune
+
+    w = synth.operator_128()
+    g = w.grid
+    cache = os.path.join(tempfile.gettempdir(), "gj_autotune_bench.json")
+    out = []
+    for prec in ("fp32", "fp64"):
+        auto = autotune.tune(g, w.mag, prec, cache=cache, reps=3)
+        for npad in ((255, 255), tuple(auto)):
+            ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
+                   gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
+            res = {"precision": prec, "npad": list(npad), "autotuned": tuple(npad) == tuple(auto),
+                   "fast_path": bool(ops[0].info.fast_path)}
+            for mode in ("cold", "warm"):
+                opl = operator_leg(torch, ops, g, dev, flush if mode == "cold" else None, hbm, steps=steps,
+                                   elem=8 if prec == "fp64" else 4)
+                res[mode] = {k: opl[k] for k in ("forward_pair_ms", "adjoint_pair_ms", "algorithmic_GBs",
+                                                 "frac_of_hbm")}
+            out.append(res)
+            for o in ops:
+                o.close()
+    return {"runs": out, "note": "both fields, standalone C-ABI calls, medians; algorithmic bytes as for the "
+                                 "256x256x40 line (spectrum bytes at the padded size in use)"}
+
+
+def oracle_c1_solve():
+    """The oracle's full FP64 dense joint RRCG on the 16x16x8 workload (50 iterations,
+    chi^2 stop off), timed end to end on one core, matrices included."""
+    import numpy as np
+    import synth
+    from oracle import operator as oop
+    from oracle import weights as owt
+    from oracle.rrcg import RRCGParams, rrcg_joint
+
+    t0 = time.perf_counter()
+    w = synth.small_joint()
+    g = w.grid
+    A = [oop.dense_matrix(g, oop.GRAVITY), oop.dense_matrix(g, oop.MAGNETIC, w.mag)]
+    obs = [owt.noisy_data(A[i] @ w.m_true[i], 0.01, 0.01, w.noise[i]) for i in range(2)]
+    wst = [owt.depth_weight_cells(g.z_edges, b, g.nx, g.ny) for b in (2.0, 3.0)]
+    t1 = time.perf_counter()
+    P = RRCGParams(p=(1, 1), lam=(50.0, 1500.0), kmax=50, stop_on_chi2=False)
+    rrcg_joint([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
+               [o[0] for o in obs], [o[1] for o in obs], [np.zeros(g.n)] * 2, wst, P)
+    t2 = time.perf_counter()
+    return {"seconds_total": t2 - t0, "seconds_solve": t2 - t1, "iterations": 50,
+            "iters_per_s": 50 / (t2 - t1), "cores": 1, "workload": "joint 16x16x8, FP64 dense, p=1, lambda=(50,1500)"}
 
 
 def batched_leg(gj, torch, dev, flush, steps=20, warmup=3):

@@ -51,7 +51,8 @@ def check(name, ref, m, rep, kmax):
     assert phi_err <= 1e-4
     for i in range(2):
         assert m_err[i] <= 1e-3, (i, m_err[i])
-        assert m[i].min() >= KW["lo"][i] and m[i].max() <= KW["hi"][i]
+        # the bounds as the FP32 path holds them (0.1 rounds up to 0.10000000149)
+        assert m[i].min() >= np.float32(KW["lo"][i]) and m[i].max() <= np.float32(KW["hi"][i])
 
 
 def test_fast_joint_solve_40_layers_against_dense_oracle():
