@@ -326,7 +326,25 @@ struct View2 {  // the two fields of a launch (field 1 unused in single-field la
     int slots;      // partial slots per column
     int nfield;
     int *err;
+    const cpx<R> *twtab;  // the column kernels' twiddle table (TabTw layout), built once per operator
 };
+
+// Every CTA of a column kernel copies the operator's twiddle table into shared
+// memory with one bulk copy (thread 0, barrier `bar`), issued before the first
+// items' copies so that both arrive together.
+template <typename R>
+__device__ __forceinline__ void load_twtab(cpx<R> *tab, const cpx<R> *src, uint64_t *bar) {
+    if (threadIdx.x == 0) {
+        mbar_expect(bar, TabTw<R>::WORDS * sizeof(cpx<R>));
+        bulk_load(tab, src, TabTw<R>::WORDS * sizeof(cpx<R>), bar);
+    }
+}
+
+// Fills the table once (one block; setup).
+template <typename R>
+__global__ void k_build_twtab(cpx<R> *tab, const cpx<R> *tw512) {
+    TabTw<R>::build(tab, tw512);
+}
 
 // ---------------------------------------------------------------------------
 // Item t = col nz + r of the column passes, column col = kx nf + fld: the fields
@@ -367,10 +385,11 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * (ZB + TB));   // 512
     C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * (ZB + TB) + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
+    __shared__ __align__(8) uint64_t tabbar;
     if (lane == 0)
         for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
+    if (threadIdx.x == 0) mbar_init(&tabbar);
     mbar_fence_init();
-    TabTw<R>::build(tab, V.op[0].twy);
     __syncthreads();
     TabTw<R> tw;
     tw.bind(tab);
@@ -379,6 +398,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     // at most T warps take part, so that every segment holds at least one item
     const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
     const long long w = (long long)blockIdx.x * CWARPS + warp;
+    // a CTA with work fetches the table; its warp 0 has work and waits for the copy,
+    // so the CTA outlives it
+    if ((long long)blockIdx.x * CWARPS < Wt) load_twtab<R>(tab, V.twtab, &tabbar);
     if (w >= Wt) return;
     const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
@@ -407,8 +429,8 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     C acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = czero<C>();
-    bool ok = true;
-    int t_fail = t1;
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&tabbar, 0, V.err));
+    int t_fail = ok ? t1 : t0;
     int seg_start = t0;
     for (int t = t0; t < t1 && ok; ++t, cu.next(nz, V.nfield)) {
         const int s = (t - t0) % CSTAGES;
@@ -506,10 +528,11 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * TB);
     C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * TB + N * sizeof(C)));
     __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
+    __shared__ __align__(8) uint64_t tabbar;
     if (lane == 0)
         for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
+    if (threadIdx.x == 0) mbar_init(&tabbar);
     mbar_fence_init();
-    TabTw<R>::build(tab, V.op[0].twy);
     __syncthreads();
     TabTw<R> tw;
     tw.bind(tab);
@@ -518,6 +541,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     // at most T warps take part, so that every segment holds at least one item
     const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
     const long long w = (long long)blockIdx.x * CWARPS + warp;
+    // a CTA with work fetches the table; its warp 0 has work and waits for the copy,
+    // so the CTA outlives it
+    if ((long long)blockIdx.x * CWARPS < Wt) load_twtab<R>(tab, V.twtab, &tabbar);
     if (w >= Wt) return;
     const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
     const int lam = 2 * l + h;
@@ -541,8 +567,8 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     if (lane == 0)
         while (ti < t1 && ti < t0 + CSTAGES) issue();
     C vh[16];
-    bool ok = true;
-    int t_fail = t1;
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&tabbar, 0, V.err));
+    int t_fail = ok ? t1 : t0;
     for (int t = t0; t < t1 && ok; ++t, cu.next(nz, V.nfield)) {
         const int r = cu.r, fld = cu.fld, kx = cu.kx;
         const OpView<R> &op = V.op[fld];

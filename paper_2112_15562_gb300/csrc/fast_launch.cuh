@@ -18,6 +18,7 @@ inline View2<R> make_view2(const gj_op *a, const gj_op *b) {
     V.slots = a->slots;
     V.nfield = b ? 2 : 1;
     V.err = a->err;
+    V.twtab = static_cast<const cpx<R> *>(a->twtab);
     return V;
 }
 

@@ -33,6 +33,7 @@ struct gj_op {
     void *P = nullptr;     // [ncol][slots][512] complex
     int *cnt = nullptr;    // [ncol] arrival counters
     int *err = nullptr;    // device error word (bounded waits)
+    void *twtab = nullptr; // the column kernels' twiddle table (FP32, TabTw layout)
     int slots = 0;
     int col_grid = 0;      // CTAs of the persistent column kernels
 };

@@ -236,8 +236,8 @@ static gj_status upload_twiddles(int N, gj_precision prec, void **out) {
 static void free_op_memory(gj_op *op) {
     if (!op) return;
     cudaFree(op->twx); cudaFree(op->twy); cudaFree(op->spec);
-    cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W); cudaFree(op->V);
-    op->twx = op->twy = op->spec = op->Z = op->Y = op->W = op->V = nullptr;
+    cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W); cudaFree(op->V); cudaFree(op->twtab);
+    op->twx = op->twy = op->spec = op->Z = op->Y = op->W = op->V = op->twtab = nullptr;
 }
 
 template <typename Rout>
@@ -423,6 +423,11 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
         op->P = op->Y;
         op->cnt = reinterpret_cast<int *>(static_cast<char *>(op->Y) + pb);
         op->err = op->cnt + 257 + 8;
+        const size_t tb = (size_t)f512::TabTw<float>::WORDS * sizeof(float2);
+        if ((e = cudaMalloc(&op->twtab, tb)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
+        f512::k_build_twtab<float><<<1, 256, 0, st>>>(static_cast<float2 *>(op->twtab),
+                                                    static_cast<const float2 *>(op->twy));
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
     }
     *out = op;
     return GJ_OK;
