@@ -384,6 +384,7 @@ def run_ours(args, rank, world, local_rank):
         line["fp64"] = fp64_leg(gj, torch, dev, flush, value, hbm, line["alu_peaks"])
         line["p2"] = p2_leg(gj, torch, ops, g, dobs, sigma, wdep, dev, flush)
         line["operator_128"] = c2_leg(gj, torch, dev, flush, hbm)
+        line["c5_512x48"] = c5_leg(gj, torch, dev, flush, hbm)
         line["e2e"] = e2e_leg(gj, torch, ops, g, dobs, sigma, wdep)
         line["batched"] = batched_leg(gj, torch, dev, flush)
         line["paper_shapes"] = paper_shapes_leg(gj, torch, dev, flush)
@@ -586,6 +587,53 @@ def c2_leg(gj, torch, dev, flush, hbm, steps=20):
                 o.close()
     return {"runs": out, "note": "both fields, standalone C-ABI calls, medians; algorithmic bytes as for the "
                                  "256x256x40 line (spectrum bytes at the padded size in use)"}
+
+
+def c5_leg(gj, torch, dev, flush, hbm):
+    """512x512 stations over 512x512x48 cells of 100 m (12.6 M cells per model), FP32,
+    padded 1024 x 1024: forward plus backward (G m through torch.autograd, backward =
+    the adjoint product) of both fields, with the layer spectra stored and with every
+    layer's spectrum rebuilt from the closed forms inside each product."""
+    import synth
+
+    g = synth.uniform_grid(512, 512, 512, 512, 48, 100.0)
+    mag = synth.Mag(50000.0, 60.0, 10.0)
+    out = {"workload": "fwd+bwd of both fields at 512x512x48 (N=1024), FP32, L2 flushed per step"}
+    for mode, steps in (("stored", 5), ("recomputed", 2)):
+        t0 = time.perf_counter()
+        ops = [gj.bttb_setup(g, "gravity", precision="fp32", recompute=mode == "recomputed"),
+               gj.bttb_setup(g, "magnetic", mag, precision="fp32", recompute=mode == "recomputed")]
+        t_setup = time.perf_counter() - t0
+        m = [torch.rand(g.n, device=dev, requires_grad=True) for _ in range(2)]
+        gd = [torch.randn(g.s, device=dev) for _ in range(2)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for k in range(steps + 1):
+            flush.fill_(float(k))
+            e0.record()
+            for i in range(2):
+                gj.G(ops[i], m[i]).backward(gd[i])
+            e1.record()
+            e1.synchronize()
+            if k >= 1:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        o = ops[0].info
+        S_mag = o.nz * o.Ny * o.ncol * 8
+        alg = 2 * 2 * (4 * g.n + 4 * g.s) + 2 * (S_mag + S_mag // 2)
+        res = {"ms_per_fwd_bwd_both_fields": ms, "setup_s": t_setup, "steps": steps,
+               "spectrum_bytes_both_fields": ops[0].info.spectrum_bytes + ops[1].info.spectrum_bytes,
+               "cells_per_s": 2 * g.n / (ms * 1e-3)}
+        if mode == "stored":
+            res["algorithmic_GBs"] = alg / (ms * 1e-3) / 1e9
+            res["frac_of_hbm"] = res["algorithmic_GBs"] / hbm
+        out[mode] = res
+        for op in ops:
+            op.close()
+        del m, gd
+        torch.cuda.empty_cache()
+    return out
 
 
 def oracle_c1_solve():

@@ -79,7 +79,8 @@ typedef struct {
     int ncol;                /* stored spectrum columns, Nx/2 + 1 */
     gj_field field;
     gj_precision precision;
-    int64_t spectrum_bytes;  /* device bytes of the stored layer spectra */
+    int64_t spectrum_bytes;  /* device bytes of the stored layer spectra (one layer when
+                                recomputed per layer) */
     int64_t workspace_bytes; /* device bytes of the per-op workspace */
     int fast_path;           /* 1: the specialised 512 x 512 kernels serve this op */
 } gj_op_info_t;
@@ -104,6 +105,28 @@ typedef struct {
 gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag,
                         gj_precision precision, int Npad_y, int Npad_x,
                         gj_stream_t stream, gj_op **out);
+
+/* Setup flags for gj_bttb_setup_ex. */
+enum {
+    /* Keep one layer's spectrum instead of all n_z: every product rebuilds each
+     * layer's spectrum from the closed-form prism fields (FP64 corner lattice of
+     * the layer's two depth planes, FP64 2-D FFT of its circulant table, rounded to
+     * the operator's precision) just before using it (Sec. 2.7.1 applied per
+     * layer).  The spectra are bit-identical to the stored ones; the cost is the
+     * setup work of one layer per layer per product.  Served by the general
+     * kernels (never the 512 x 512 fast path); products only: the joint solver
+     * rejects such operators with GJ_ERR_UNSUPPORTED. */
+    GJ_SETUP_RECOMPUTE_SPECTRA = 1
+};
+
+/*
+ * gj_bttb_setup_ex - gj_bttb_setup with setup flags (0 or
+ * GJ_SETUP_RECOMPUTE_SPECTRA); gj_bttb_setup(...) equals gj_bttb_setup_ex(...,
+ * 0, ...).  Unknown flags return GJ_ERR_ARG.
+ */
+gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const gj_mag *mag,
+                           gj_precision precision, int Npad_y, int Npad_x, int flags,
+                           gj_stream_t stream, gj_op **out);
 
 /* Sizes of an operator (host struct filled synchronously). */
 gj_status gj_op_info(const gj_op *op, gj_op_info_t *info);

@@ -14,6 +14,7 @@ STATUS_CODE = {v: k for k, v in STATUS.items()}
 GJ_GRAVITY, GJ_MAGNETIC = 1, 2
 GJ_FP64, GJ_FP32_MIXED = 0, 1
 GJ_SCALARS_AUTO, GJ_SCALARS_JOINT, GJ_SCALARS_PER_FIELD = 0, 1, 2
+GJ_SETUP_RECOMPUTE_SPECTRA = 1
 
 
 class GJError(RuntimeError):
@@ -73,6 +74,7 @@ def load() -> ct.CDLL:
     pp = ct.POINTER(vp)
     sig = {
         "gj_bttb_setup": (i32, [ct.POINTER(Grid), i32, ct.POINTER(Mag), i32, i32, i32, vp, pp]),
+        "gj_bttb_setup_ex": (i32, [ct.POINTER(Grid), i32, ct.POINTER(Mag), i32, i32, i32, i32, vp, pp]),
         "gj_op_info": (i32, [vp, ct.POINTER(OpInfo)]),
         "gj_op_destroy": (None, [vp]),
         "gj_op_status": (i32, [vp, i32, vp]),

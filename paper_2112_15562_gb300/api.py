@@ -65,9 +65,10 @@ class Op:
             pass
 
 
-def bttb_setup(grid, field, mag=None, precision="fp32", npad=(0, 0), stream=None) -> Op:
-    """gj_bttb_setup: ``grid`` has sx, sy, nx, ny, nz, dx, dy, z_edges[, station_z, off_x, off_y];
-    ``mag`` has F, incl, decl (magnetic only)."""
+def bttb_setup(grid, field, mag=None, precision="fp32", npad=(0, 0), stream=None, recompute=False) -> Op:
+    """gj_bttb_setup_ex: ``grid`` has sx, sy, nx, ny, nz, dx, dy, z_edges[, station_z, off_x, off_y];
+    ``mag`` has F, incl, decl (magnetic only); ``recompute`` keeps one layer's spectrum and
+    rebuilds each layer's spectrum in every product (GJ_SETUP_RECOMPUTE_SPECTRA)."""
     lib = load()
     z = np.ascontiguousarray(np.asarray(grid.z_edges, dtype=np.float64))
     g = L.Grid(int(grid.sx), int(grid.sy), int(grid.nx), int(grid.ny), int(grid.nz), float(grid.dx),
@@ -77,8 +78,9 @@ def bttb_setup(grid, field, mag=None, precision="fp32", npad=(0, 0), stream=None
     if mag is not None:
         m = L.Mag(float(mag.F), float(mag.incl), float(mag.decl))
     out = ct.c_void_p()
-    check(lib.gj_bttb_setup(ct.byref(g), _FIELD[field], ct.byref(m) if m is not None else None,
-                            _PREC[precision], int(npad[0]), int(npad[1]), _stream(stream), ct.byref(out)))
+    check(lib.gj_bttb_setup_ex(ct.byref(g), _FIELD[field], ct.byref(m) if m is not None else None,
+                               _PREC[precision], int(npad[0]), int(npad[1]),
+                               L.GJ_SETUP_RECOMPUTE_SPECTRA if recompute else 0, _stream(stream), ct.byref(out)))
     info = L.OpInfo()
     check(lib.gj_op_info(out, ct.byref(info)))
     return Op(out.value, info)

@@ -28,6 +28,8 @@ struct OpView {
     cpx<R> *W;           // [max(sy, ...)][ncol]  inverse-column output / residual rows
     cpx<R> *V;           // fast path: residual-row spectra [ncol][256] (unused otherwise)
     int real_spec;       // fast path: spec holds only real parts, R[nz][ncol][Ny] (even table)
+    int rbase;           // first layer of a column launch (per-layer launches of the recompute mode)
+    int spec_r0;         // layer held at spec index 0 (0 when all layers are stored)
 };
 
 // How real lines are paired into complex transforms.
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(256) k_col_fwd_mac(OpView<R> op0, OpView<R> op
     if (stopped(done)) return;
     const OpView<R> &op = blockIdx.z ? op1 : op0;
     const int c0 = blockIdx.x * C;
-    const int r0 = blockIdx.y * L;
+    const int r0 = op.rbase + blockIdx.y * L;
     if (r0 >= op.nz || c0 >= op.ncol) return;
     const int r1 = min(r0 + L, op.nz);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(256) k_col_fwd_mac(OpView<R> op0, OpView<R> op
         }
         __syncthreads();
         const Cx *X = fft_lines<R, false>(buf0, buf1, op.py, C, tw, ny);
-        const Cx *Tr = op.spec + (size_t)r * Ny * ncol;
+        const Cx *Tr = op.spec + (size_t)(r - op.spec_r0) * Ny * ncol;
         for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
             const int c = it % C, ky = it / C;
             if (c0 + c < ncol) acc[it] = cadd(acc[it], cmul(X[it], Tr[(size_t)ky * ncol + c0 + c]));
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(256) k_col_adj(OpView<R> op0, OpView<R> op1, i
     if (stopped(done)) return;
     const OpView<R> &op = blockIdx.z ? op1 : op0;
     const int c0 = blockIdx.x * C;
-    const int r = blockIdx.y;
+    const int r = op.rbase + blockIdx.y;
     if (c0 >= op.ncol || r >= op.nz) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ny = op.Ny, ncol = op.ncol, ny = op.ny;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256) k_col_adj(OpView<R> op0, OpView<R> op1, i
     Cx *buf1 = buf0 + Ny * C;
     Cx *tw = buf1 + Ny * C;
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
-    const Cx *Tr = op.spec + (size_t)r * Ny * ncol;
+    const Cx *Tr = op.spec + (size_t)(r - op.spec_r0) * Ny * ncol;
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
         const int c = it % C, ky = it / C;
         buf0[it] = (c0 + c < ncol) ? cmulc(op.Y[(size_t)ky * ncol + c0 + c], Tr[(size_t)ky * ncol + c0 + c])

@@ -8,6 +8,8 @@
 #include "../../include/gj.h"
 #include "fft.cuh"
 
+namespace gj { struct gj_setup_scratch_impl; }
+
 struct gj_op {
     // geometry
     int sx, sy, nx, ny, nz, off_x, off_y;
@@ -34,6 +36,10 @@ struct gj_op {
     int *cnt = nullptr;    // [ncol] arrival counters
     int *err = nullptr;    // device error word (bounded waits)
     void *twtab = nullptr; // the column kernels' twiddle table (FP32, TabTw layout)
+    // per-layer spectrum recomputation (GJ_SETUP_RECOMPUTE_SPECTRA): `spec` holds one
+    // layer, rebuilt from the closed forms before each use
+    bool recompute = false;
+    gj::gj_setup_scratch_impl *scratch = nullptr;
     int slots = 0;
     int col_grid = 0;      // CTAs of the persistent column kernels
 };
@@ -57,6 +63,9 @@ template <typename R> OpView<R> view_of(const gj_op *op);
 // fast-path helpers (setup.cu)
 bool fast_eligible(const gj_op *op);
 int fast_slots(int nfield, int nz, int grid_ctas);
+
+// rebuilds layer r's spectrum into spec (recompute mode; setup.cu)
+void recompute_layer(const gj_op *op, int r, cudaStream_t st);
 
 // enqueue products (matvec.cu)
 gj_status forward_enqueue(const gj_op *op, const void *m, void *d, cudaStream_t s);

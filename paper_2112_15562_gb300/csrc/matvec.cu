@@ -23,7 +23,18 @@ static void launch_forward(const gj_op *o, const R *m, R *d, cudaStream_t st) {
     const int nt = (o->ncol + C - 1) / C;
     const size_t msm = col_smem(o->Ny, C, 3, cs);
     allow_max_smem(k_col_fwd_mac<R>);
-    k_col_fwd_mac<R><<<dim3(nt, (o->nz + o->L_grp - 1) / o->L_grp, 1), 256, msm, st>>>(v, v, C, o->L_grp, nullptr);
+    if (o->recompute) {
+        // one layer at a time: rebuild its spectrum, then add its column products
+        for (int r = 0; r < o->nz; ++r) {
+            recompute_layer(o, r, st);
+            OpView<R> vr = v;
+            vr.rbase = r;
+            vr.spec_r0 = r;
+            k_col_fwd_mac<R><<<dim3(nt, 1, 1), 256, msm, st>>>(vr, vr, C, 1, nullptr);
+        }
+    } else {
+        k_col_fwd_mac<R><<<dim3(nt, (o->nz + o->L_grp - 1) / o->L_grp, 1), 256, msm, st>>>(v, v, C, o->L_grp, nullptr);
+    }
     // inverse columns
     const size_t ism = col_smem(o->Ny, C, 2, cs);
     allow_max_smem(k_col_inv<R>);
@@ -54,7 +65,17 @@ static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
     allow_max_smem(k_col_fft<R>);
     k_col_fft<R><<<dim3(nt, 1), 256, sm2, st>>>(v, v, C, nullptr);
     allow_max_smem(k_col_adj<R>);
-    k_col_adj<R><<<dim3(nt, o->nz, 1), 256, sm2, st>>>(v, v, C, nullptr);
+    if (o->recompute) {
+        for (int r = 0; r < o->nz; ++r) {
+            recompute_layer(o, r, st);
+            OpView<R> vr = v;
+            vr.rbase = r;
+            vr.spec_r0 = r;
+            k_col_adj<R><<<dim3(nt, 1, 1), 256, sm2, st>>>(vr, vr, C, nullptr);
+        }
+    } else {
+        k_col_adj<R><<<dim3(nt, o->nz, 1), 256, sm2, st>>>(v, v, C, nullptr);
+    }
     PairMap pm{o->nz * o->ny, 0};
     const int npr = (pm.nlines + 1) / 2;
     allow_max_smem(k_row_inv<R, StorePlain<R>>);

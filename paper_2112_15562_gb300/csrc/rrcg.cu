@@ -888,6 +888,10 @@ static gj_status check_ops(const gj_op *const ops[2]) {
         a->Nx != b->Nx || a->Ny != b->Ny || a->prec != b->prec) {
         set_error("rrcg: both operators must share grid sizes, padded sizes and precision"); return GJ_ERR_ARG;
     }
+    if (a->recompute || b->recompute) {
+        set_error("rrcg: operators that recompute their spectra per layer serve products only");
+        return GJ_ERR_UNSUPPORTED;
+    }
     return GJ_OK;
 }
 

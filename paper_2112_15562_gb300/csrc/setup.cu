@@ -233,52 +233,82 @@ static gj_status upload_twiddles(int N, gj_precision prec, void **out) {
     return GJ_OK;
 }
 
+struct gj_setup_scratch_impl;
+static void scratch_free(gj_setup_scratch_impl *sc);
+
 static void free_op_memory(gj_op *op) {
     if (!op) return;
+    scratch_free(op->scratch);
+    op->scratch = nullptr;
     cudaFree(op->twx); cudaFree(op->twy); cudaFree(op->spec);
     cudaFree(op->Z); cudaFree(op->Y); cudaFree(op->W); cudaFree(op->V); cudaFree(op->twtab);
     op->twx = op->twy = op->spec = op->Z = op->Y = op->W = op->V = op->twtab = nullptr;
 }
 
-template <typename Rout>
-static gj_status build_spectra(gj_op *op, cudaStream_t st) {
-    // FP64 twiddles for the setup transforms
-    void *twx64 = nullptr, *twy64 = nullptr;
+// Work buffers of the spectrum build for `layers` consecutive layers: the FP64
+// corner lattice (layers + 1 depth planes), the FP64 row-pass output, the depths
+// and FP64 twiddles.  Kept by operators that rebuild their spectra per layer.
+struct gj_setup_scratch_impl {
     double *lat = nullptr;
     double2 *Zs = nullptr;
+    double *zw = nullptr;
+    void *twx64 = nullptr, *twy64 = nullptr;
+    bool own_tw = false;
+    int layers = 0;
+};
+
+static void scratch_free(gj_setup_scratch_impl *sc) {
+    if (!sc) return;
+    cudaFree(sc->lat); cudaFree(sc->Zs); cudaFree(sc->zw);
+    if (sc->own_tw) { cudaFree(sc->twx64); cudaFree(sc->twy64); }
+    delete sc;
+}
+
+static gj_status scratch_alloc(const gj_op *op, int layers, gj_setup_scratch_impl **out) {
+    gj_setup_scratch_impl *sc = new (std::nothrow) gj_setup_scratch_impl();
+    if (!sc) { set_error("setup scratch: host allocation failed"); return GJ_ERR_OOM; }
+    sc->layers = layers;
     gj_status rc = GJ_OK;
-    auto cleanup = [&]() {
-        cudaFree(lat); cudaFree(Zs);
-        if (op->prec != GJ_FP64) { cudaFree(twx64); cudaFree(twy64); }
-    };
+    cudaError_t e;
     if (op->prec == GJ_FP64) {
-        twx64 = op->twx;
-        twy64 = op->twy;
+        sc->twx64 = op->twx;
+        sc->twy64 = op->twy;
     } else {
-        if ((rc = upload_twiddles(op->Nx, GJ_FP64, &twx64)) != GJ_OK) { cleanup(); return rc; }
-        if ((rc = upload_twiddles(op->Ny, GJ_FP64, &twy64)) != GJ_OK) { cleanup(); return rc; }
+        sc->own_tw = true;
+        if ((rc = upload_twiddles(op->Nx, GJ_FP64, &sc->twx64)) != GJ_OK) { scratch_free(sc); return rc; }
+        if ((rc = upload_twiddles(op->Ny, GJ_FP64, &sc->twy64)) != GJ_OK) { scratch_free(sc); return rc; }
     }
+    const size_t plane = (size_t)(op->sx + op->nx) * (op->sy + op->ny);
+    std::vector<double> zw(op->nz + 1);
+    for (int k = 0; k <= op->nz; ++k) zw[k] = op->z_edges[k] - op->station_z;
+    if ((e = cudaMalloc(&sc->lat, plane * (layers + 1) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&sc->Zs, (size_t)layers * op->Ny * op->ncol * sizeof(double2))) != cudaSuccess ||
+        (e = cudaMalloc(&sc->zw, zw.size() * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemcpy(sc->zw, zw.data(), zw.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        scratch_free(sc);
+        return cuda_fail(e, "setup scratch");
+    }
+    *out = sc;
+    return GJ_OK;
+}
+
+// Spectra of layers r0 .. r0 + count - 1 (count <= the scratch's layers) into
+// spec[0 .. count): corner lattice of the count + 1 depth planes, the circulant
+// embedding of each layer's table differenced from it while loading the FP64 row
+// transforms, FP64 column transforms, rounding to the operator's precision.
+// Enqueues only (no synchronisation).
+template <typename Rout>
+static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r0, int count, cpx<Rout> *spec,
+                         cudaStream_t st) {
     Lattice L;
     L.b_max = op->off_x + op->sx - 1;
     L.a_max = op->off_y + op->sy - 1;
     L.nbx1 = op->sx + op->nx;
     L.nby1 = op->sy + op->ny;
-    L.nz1 = op->nz + 1;
+    L.nz1 = count + 1;
     L.dx = op->dx;
     L.dy = op->dy;
-    std::vector<double> zw(op->nz + 1);
-    for (int k = 0; k <= op->nz; ++k) zw[k] = op->z_edges[k] - op->station_z;
-    double *zw_d = nullptr;
-    const size_t nlat = (size_t)L.nbx1 * L.nby1 * L.nz1;
-    cudaError_t e;
-    if ((e = cudaMalloc(&lat, nlat * sizeof(double))) != cudaSuccess) { cleanup(); return cuda_fail(e, "lattice"); }
-    if ((e = cudaMalloc(&Zs, (size_t)op->nz * op->Ny * op->ncol * sizeof(double2))) != cudaSuccess) {
-        cleanup(); return cuda_fail(e, "setup rows");
-    }
-    if ((e = cudaMalloc(&zw_d, zw.size() * sizeof(double))) != cudaSuccess) { cleanup(); return cuda_fail(e, "zw"); }
-    cudaMemcpy(zw_d, zw.data(), zw.size() * sizeof(double), cudaMemcpyHostToDevice);
-    L.zw = zw_d;
-
+    L.zw = sc.zw + r0;
     MagCoef mc{};
     double scale = 1.0 / ((double)op->Nx * (double)op->Ny);
     const int magnetic = op->field == GJ_MAGNETIC;
@@ -293,46 +323,65 @@ static gj_status build_spectra(gj_op *op, cudaStream_t st) {
         // G = 6.6743e-11 m^3 kg^-1 s^-2; g/cc -> kg/m^3 (1e3); m/s^2 -> mGal (1e5)
         scale *= 6.6743e-11 * 1.0e3 * 1.0e5;
     }
-    k_corner_lattice<<<1216, 256, 0, st>>>(L, magnetic, mc, lat);
+    k_corner_lattice<<<1216, 256, 0, st>>>(L, magnetic, mc, sc.lat);
 
     OpView<double> v{};
-    v.sx = op->sx; v.sy = op->sy; v.nx = op->nx; v.ny = op->ny; v.nz = op->nz;
+    v.sx = op->sx; v.sy = op->sy; v.nx = op->nx; v.ny = op->ny; v.nz = count;
     v.Nx = op->Nx; v.Ny = op->Ny; v.ncol = op->ncol; v.px = op->px; v.py = op->py;
-    v.twx = static_cast<const double2 *>(twx64);
-    v.twy = static_cast<const double2 *>(twy64);
+    v.twx = static_cast<const double2 *>(sc.twx64);
+    v.twy = static_cast<const double2 *>(sc.twy64);
 
     LoadTable lt;
-    lt.lat = lat; lt.nbx1 = L.nbx1; lt.nby1 = L.nby1;
+    lt.lat = sc.lat; lt.nbx1 = L.nbx1; lt.nby1 = L.nby1;
     lt.Nx = op->Nx; lt.Ny = op->Ny; lt.sx = op->sx; lt.sy = op->sy; lt.nx = op->nx; lt.ny = op->ny;
     lt.off_x = op->off_x; lt.off_y = op->off_y; lt.a_max = L.a_max; lt.b_max = L.b_max;
     lt.scale = scale;
-    PairMap pm{op->nz * op->Ny, 0};
+    PairMap pm{count * op->Ny, 0};
     const int P = pick_row_pairs(op->Nx, sizeof(double2));
     const int npairs = (pm.nlines + 1) / 2;
     const size_t rsm = row_smem(op->Nx, P, sizeof(double2));
-    allow_max_smem(k_row_fwd<double, LoadTable>);
-    k_row_fwd<double, LoadTable><<<(npairs + P - 1) / P, 256, rsm, st>>>(v, pm, op->Nx, P, Zs, Zs, lt, nullptr);
+    k_row_fwd<double, LoadTable><<<(npairs + P - 1) / P, 256, rsm, st>>>(v, pm, op->Nx, P, sc.Zs, sc.Zs, lt, nullptr);
     const int C = pick_col_tile(op->Ny, sizeof(double2), 2);
     const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
-    allow_max_smem(k_col_spec<Rout>);
-    dim3 g((op->ncol + C - 1) / C, op->nz);
-    k_col_spec<Rout><<<g, 256, csm, st>>>(v, Zs, static_cast<cpx<Rout> *>(op->spec), C, op->fast ? 1 : 0,
-                                         op->real_spec ? 1 : 0);
-    e = cudaGetLastError();
+    dim3 g((op->ncol + C - 1) / C, count);
+    k_col_spec<Rout><<<g, 256, csm, st>>>(v, sc.Zs, spec, C, op->fast ? 1 : 0, op->real_spec ? 1 : 0);
+}
+
+static void set_build_attributes() {
+    allow_max_smem(k_row_fwd<double, LoadTable>);
+    allow_max_smem(k_col_spec<float>);
+    allow_max_smem(k_col_spec<double>);
+}
+
+template <typename Rout>
+static gj_status build_spectra(gj_op *op, cudaStream_t st) {
+    gj_setup_scratch_impl *sc = nullptr;
+    gj_status rc = scratch_alloc(op, op->nz, &sc);
+    if (rc != GJ_OK) return rc;
+    set_build_attributes();
+    build_layers<Rout>(op, *sc, 0, op->nz, static_cast<cpx<Rout> *>(op->spec), st);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(zw_d);
-    cleanup();
+    scratch_free(sc);
     if (e != cudaSuccess) return cuda_fail(e, "spectra setup");
     return GJ_OK;
+}
+
+void recompute_layer(const gj_op *op, int r, cudaStream_t st) {
+    if (op->prec == GJ_FP64)
+        build_layers<double>(op, *op->scratch, r, 1, static_cast<cpx<double> *>(op->spec), st);
+    else
+        build_layers<float>(op, *op->scratch, r, 1, static_cast<cpx<float> *>(op->spec), st);
 }
 
 }  // namespace gj
 
 using namespace gj;
 
-extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag, gj_precision prec,
-                                   int Npad_y, int Npad_x, gj_stream_t stream, gj_op **out) {
+extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const gj_mag *mag, gj_precision prec,
+                                      int Npad_y, int Npad_x, int flags, gj_stream_t stream, gj_op **out) {
     if (!out) { set_error("gj_bttb_setup: out is NULL"); return GJ_ERR_ARG; }
+    if (flags & ~GJ_SETUP_RECOMPUTE_SPECTRA) { set_error("gj_bttb_setup_ex: unknown flags"); return GJ_ERR_ARG; }
     *out = nullptr;
     if (!grid) { set_error("gj_bttb_setup: grid is NULL"); return GJ_ERR_ARG; }
     const gj_grid &G = *grid;
@@ -375,7 +424,8 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     op->P_row = pick_row_pairs(Nx, cs);
     op->C_col = pick_col_tile(Ny, cs, 3);
     op->L_grp = 4;
-    op->fast = fast_eligible(op);
+    op->recompute = (flags & GJ_SETUP_RECOMPUTE_SPECTRA) != 0;
+    op->fast = !op->recompute && fast_eligible(op);
     if (op->fast) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -391,10 +441,16 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     cudaError_t e;
     if ((rc = upload_twiddles(Nx, prec, &op->twx)) != GJ_OK) goto fail;
     if ((rc = upload_twiddles(Ny, prec, &op->twy)) != GJ_OK) goto fail;
-    op->spec_bytes = (size_t)G.nz * Ny * op->ncol * (op->real_spec ? cs / 2 : cs);
+    op->spec_bytes = (size_t)(op->recompute ? 1 : G.nz) * Ny * op->ncol * (op->real_spec ? cs / 2 : cs);
     if ((e = cudaMalloc(&op->spec, op->spec_bytes)) != cudaSuccess) { rc = cuda_fail(e, "spectra"); goto fail; }
-    rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
-    if (rc != GJ_OK) goto fail;
+    if (op->recompute) {
+        // one layer's spectrum plus the build's work buffers for one layer, kept
+        if ((rc = scratch_alloc(op, 1, &op->scratch)) != GJ_OK) goto fail;
+        set_build_attributes();
+    } else {
+        rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
+        if (rc != GJ_OK) goto fail;
+    }
     if (!op->fast) {
         const size_t zb = (size_t)G.nz * G.ny * op->ncol * cs;
         const size_t yb = (size_t)Ny * op->ncol * cs;
@@ -435,6 +491,11 @@ fail:
     free_op_memory(op);
     delete op;
     return rc;
+}
+
+extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj_mag *mag, gj_precision prec,
+                                   int Npad_y, int Npad_x, gj_stream_t stream, gj_op **out) {
+    return gj_bttb_setup_ex(grid, field, mag, prec, Npad_y, Npad_x, 0, stream, out);
 }
 
 extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {

@@ -19,6 +19,8 @@ inline OpView<R> view_of(const gj_op *op) {
     v.W = static_cast<cpx<R> *>(op->W);
     v.V = static_cast<cpx<R> *>(op->V);
     v.real_spec = op->real_spec ? 1 : 0;
+    v.rbase = 0;
+    v.spec_r0 = 0;
     return v;
 }
 

@@ -1,0 +1,102 @@
+"""Per-layer spectrum recomputation (GJ_SETUP_RECOMPUTE_SPECTRA) and the 512x512x48
+workload on a 1024 x 1024 embedding (Sec. 2.7.1, Eq. d=gm).
+
+* Small grids: products of operators that rebuild each layer's spectrum before use
+  equal the dense FP64 oracle within the usual tolerances and equal the stored-spectra
+  operators (the spectra are bit-identical; the forward's layer sums may round in
+  another order).
+* 512x512 stations over 512x512x48 cells of 100 m (12.6 M cells per model), FP32,
+  padded 1024 x 1024: sampled forward rows and adjoint cells of both fields, with
+  stored and with recomputed spectra, against the oracle's dense rows and columns
+  (closed-form prism fields for every cell or station).  The errors are printed
+  (run with -s)."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import operator as oop
+from tests.gpu_common import TOL, lib, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MAG = synth.Mag(50000.0, 60.0, 10.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("npad", [(0, 0), (25, 21)])
+def test_recompute_matches_stored_and_oracle(prec, npad):
+    gj = lib()
+    g = synth.uniform_grid(12, 10, 12, 10, 5, 40.0)
+    rng = np.random.default_rng(31)
+    for field, f in (("gravity", oop.GRAVITY), ("magnetic", oop.MAGNETIC)):
+        A = oop.dense_matrix(g, f, MAG)
+        mag = MAG if field == "magnetic" else None
+        st = gj.bttb_setup(g, field, mag, precision=prec, npad=npad)
+        rc = gj.bttb_setup(g, field, mag, precision=prec, npad=npad, recompute=True)
+        assert rc.info.spectrum_bytes * g.nz == st.info.spectrum_bytes
+        m = rng.standard_normal(g.n)
+        r = rng.standard_normal(g.s)
+        d_s, d_r = st.forward(to_dev(m, prec)).cpu().numpy(), rc.forward(to_dev(m, prec)).cpu().numpy()
+        a_s, a_r = st.adjoint(to_dev(r, prec)).cpu().numpy(), rc.adjoint(to_dev(r, prec)).cpu().numpy()
+        assert rel(d_r, A @ m) <= TOL[prec] and rel(a_r, A.T @ r) <= TOL[prec]
+        assert np.array_equal(a_r, a_s)  # per-layer products from identical spectra
+        assert rel(d_r, d_s) <= (1e-13 if prec == "fp64" else 1e-6)
+
+
+def test_recompute_operator_is_rejected_by_the_solver():
+    gj = lib()
+    g = synth.uniform_grid(8, 8, 8, 8, 3, 40.0)
+    ops = [gj.bttb_setup(g, "gravity", precision="fp64", recompute=True), gj.bttb_setup(g, "magnetic", MAG,
+                                                                                         precision="fp64")]
+    with pytest.raises(gj.GJError) as ei:
+        gj.Solver(ops, gj.solver_params(kmax=2), [to_dev(np.ones(g.s), "fp64")] * 2, [to_dev(np.ones(g.s), "fp64")] * 2,
+                  [to_dev(np.ones(g.nz), "fp64")] * 2, [to_dev(np.zeros(g.n), "fp64") for _ in range(2)])
+    assert ei.value.status == -6  # GJ_ERR_UNSUPPORTED
+
+
+def _dense_row(g, j, f):
+    jy, jx = divmod(int(j), g.sx)
+    sub = copy.copy(g)
+    sub.sx, sub.sy, sub.off_x, sub.off_y = 1, 1, g.off_x + jx, g.off_y + jy
+    return oop.dense_matrix(sub, f, MAG)[0]
+
+
+def _dense_col(g, c, f):
+    r, rem = divmod(int(c), g.nx * g.ny)
+    iy, ix = divmod(rem, g.nx)
+    sub = copy.copy(g)
+    sub.nx, sub.ny, sub.nz = 1, 1, 1
+    sub.off_x, sub.off_y = g.off_x - ix, g.off_y - iy
+    sub.z_edges = g.z_edges[r:r + 2].copy()
+    return oop.dense_matrix(sub, f, MAG)[:, 0]
+
+
+def test_512x48_on_a_1024_embedding_sampled():
+    gj = lib()
+    g = synth.uniform_grid(512, 512, 512, 512, 48, 100.0)
+    m = {f: synth.smooth_blocky(g, v, 5 + f, n_boxes=6, sigma=12.0) for f, v in ((1, 1.0), (2, 0.1))}
+    rng = np.random.default_rng(55)
+    r = rng.standard_normal(g.s)
+    rows = [3 * 512 + 7, 300 * 512 + 401]
+    cells = [0, g.n - 1, 17 * 262144 + 200 * 512 + 100, 40 * 262144 + 5 * 512 + 480]
+    for field, f in (("gravity", oop.GRAVITY), ("magnetic", oop.MAGNETIC)):
+        mag = MAG if field == "magnetic" else None
+        ref_d = np.array([_dense_row(g, j, f) @ m[f] for j in rows])
+        ref_a = np.array([_dense_col(g, c, f) @ r for c in cells])
+        out = {}
+        for mode in ("stored", "recomputed"):
+            op = gj.bttb_setup(g, field, mag, precision="fp32", recompute=(mode == "recomputed"))
+            assert op.info.Nx == 1024 and op.info.Ny == 1024 and op.info.fast_path == 0
+            d = op.forward(to_dev(m[f], "fp32")).cpu().numpy()
+            a = op.adjoint(to_dev(r, "fp32")).cpu().numpy()
+            op.close()
+            ed, ea = rel(d[rows], ref_d), rel(a[cells], ref_a)
+            print(f"\n512x512x48 N=1024 {field} {mode}: sampled forward rel {ed:.2e}, sampled adjoint rel {ea:.2e}")
+            assert ed <= TOL["fp32"] and ea <= TOL["fp32"], (field, mode, ed, ea)
+            out[mode] = (d, a)
+        assert np.array_equal(out["stored"][1], out["recomputed"][1])
+        assert rel(out["recomputed"][0], out["stored"][0]) <= 1e-6
+        torch.cuda.empty_cache()
