@@ -571,11 +571,15 @@ def c2_leg(gj, torch, dev, flush, hbm, steps=20):
     cache = os.path.join(tempfile.gettempdir(), "gj_autotune_bench.json")
     out = []
     for prec in ("fp32", "fp64"):
-        auto = autotune.tune(g, w.mag, prec, cache=cache, reps=3)
+        auto, tiles = autotune.tune_full(g, w.mag, prec, cache=cache, reps=3)
         for npad in ((255, 255), tuple(auto)):
             ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
                    gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
-            res = {"precision": prec, "npad": list(npad), "autotuned": tuple(npad) == tuple(auto),
+            tuned = tuple(npad) == tuple(auto)
+            for o_ in ops:
+                if tuned and tiles:
+                    o_.tune(**tiles)
+            res = {"precision": prec, "npad": list(npad), "autotuned": tuned, "tiles": tiles if tuned else {},
                    "fast_path": bool(ops[0].info.fast_path)}
             for mode in ("cold", "warm"):
                 opl = operator_leg(torch, ops, g, dev, flush if mode == "cold" else None, hbm, steps=steps,
@@ -676,10 +680,13 @@ def batched_leg(gj, torch, dev, flush, steps=20, warmup=3):
     for i, (nx, ny, nz) in enumerate(sizes):
         gr = synth.uniform_grid(nx, ny, nx, ny, nz, 100.0)
         mag = synth.Mag(50000.0, 60.0, 10.0)
-        npad = autotune.tune(gr, mag, "fp32", cache=cache, reps=3)
-        npads.append(list(npad))
+        npad, tiles = autotune.tune_full(gr, mag, "fp32", cache=cache, reps=3)
+        npads.append(list(npad) + ([tiles] if tiles else []))
         ops = [gj.bttb_setup(gr, "gravity", precision="fp32", npad=npad),
                gj.bttb_setup(gr, "magnetic", mag, precision="fp32", npad=npad)]
+        for o_ in ops:
+            if tiles:
+                o_.tune(**tiles)
         mt = [torch.from_numpy(synth.dipping_blocks(gr, v, 40 + i)).float().to(dev) for v in (1.0, 0.1)]
         d = [ops[k].forward(mt[k]) for k in range(2)]
         sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
@@ -738,9 +745,12 @@ def paper_shapes_leg(gj, torch, dev, flush, steps=20, warmup=3):
     for name, (nx, ny, nz), (dh, dz), laptop in PAPER_SHAPES:
         gr = synth.uniform_grid(nx, ny, nx, ny, nz, dh, dz=dz)
         mag = synth.Mag(50000.0, 45.0, 45.0)
-        npad = autotune.tune(gr, mag, "fp32", cache=cache, reps=3)
+        npad, tiles = autotune.tune_full(gr, mag, "fp32", cache=cache, reps=3)
         ops = [gj.bttb_setup(gr, "gravity", precision="fp32", npad=npad),
                gj.bttb_setup(gr, "magnetic", mag, precision="fp32", npad=npad)]
+        for o_ in ops:
+            if tiles:
+                o_.tune(**tiles)
         mt = [torch.from_numpy(synth.dipping_blocks(gr, v, 7)).float().to(dev) for v in (1.0, 0.1)]
         d = [ops[k].forward(mt[k]) for k in range(2)]
         sig = [0.01 * x.abs() + 0.01 * x.abs().max() for x in d]
@@ -751,7 +761,7 @@ def paper_shapes_leg(gj, torch, dev, flush, steps=20, warmup=3):
         ts, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
         sv.close()
         s_it = sum(ts) / steps / 1e3
-        out.append({"workload": name, "npad": list(npad), "s_per_iter": s_it, "laptop_s_per_iter": laptop,
+        out.append({"workload": name, "npad": list(npad), "tiles": tiles, "s_per_iter": s_it, "laptop_s_per_iter": laptop,
                     "ratio_vs_laptop": laptop / s_it})
     return {"runs": out, "note": "laptop figures: the paper's Intel i7-10750H, FP64, total time / iterations; "
                                  "a different machine and workload (context, not a target)"}

@@ -83,6 +83,9 @@ typedef struct {
                                 recomputed per layer) */
     int64_t workspace_bytes; /* device bytes of the per-op workspace */
     int fast_path;           /* 1: the specialised 512 x 512 kernels serve this op */
+    int P_row, C_col, L_grp; /* launch shapes of the general kernels (gj_op_tune) */
+    int radix_order;         /* radix plan of the general kernels' transforms (gj_op_tune) */
+    int recompute;           /* 1: spectra rebuilt per layer (GJ_SETUP_RECOMPUTE_SPECTRA) */
 } gj_op_info_t;
 
 /*
@@ -130,6 +133,19 @@ gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const gj_mag *ma
 
 /* Sizes of an operator (host struct filled synchronously). */
 gj_status gj_op_info(const gj_op *op, gj_op_info_t *info);
+
+/*
+ * gj_op_tune - launch shapes of the general (non-512) product kernels, the knobs
+ * of the autotuner (the paper has no counterpart).  P_row: line pairs per CTA of
+ * the row passes; C_col: columns per CTA of the column passes; L_grp: layers per
+ * CTA of the layer-summed spectrum multiply; radix_order: the radix plan of the
+ * transforms (0: radix 8 first, then the odd primes ascending; 1: the same stages
+ * reversed; 2: radix 4 for the power-of-two part).  A value <= 0 (or < 0 for
+ * radix_order) keeps the current choice.  Any choice gives the same products up
+ * to rounding.  Synchronous, host-side only; GJ_ERR_ARG if a tile does not fit
+ * in shared memory.  Not for operators in use on another stream.
+ */
+gj_status gj_op_tune(gj_op *op, int P_row, int C_col, int L_grp, int radix_order);
 
 /* Frees an operator (waits for the device to finish using it).  NULL is a no-op. */
 void gj_op_destroy(gj_op *op);

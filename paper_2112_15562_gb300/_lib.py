@@ -37,7 +37,8 @@ class OpInfo(ct.Structure):
     _fields_ = [("sx", ct.c_int), ("sy", ct.c_int), ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
                 ("Nx", ct.c_int), ("Ny", ct.c_int), ("ncol", ct.c_int), ("field", ct.c_int),
                 ("precision", ct.c_int), ("spectrum_bytes", ct.c_int64), ("workspace_bytes", ct.c_int64),
-                ("fast_path", ct.c_int)]
+                ("fast_path", ct.c_int), ("P_row", ct.c_int), ("C_col", ct.c_int), ("L_grp", ct.c_int),
+                ("radix_order", ct.c_int), ("recompute", ct.c_int)]
 
 
 class RRCGParams(ct.Structure):
@@ -76,6 +77,7 @@ def load() -> ct.CDLL:
         "gj_bttb_setup": (i32, [ct.POINTER(Grid), i32, ct.POINTER(Mag), i32, i32, i32, vp, pp]),
         "gj_bttb_setup_ex": (i32, [ct.POINTER(Grid), i32, ct.POINTER(Mag), i32, i32, i32, i32, vp, pp]),
         "gj_op_info": (i32, [vp, ct.POINTER(OpInfo)]),
+        "gj_op_tune": (i32, [vp, i32, i32, i32, i32]),
         "gj_op_destroy": (None, [vp]),
         "gj_op_status": (i32, [vp, i32, vp]),
         "gj_selftest_bounded_wait": (i32, [i64, vp]),

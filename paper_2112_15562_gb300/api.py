@@ -53,6 +53,16 @@ class Op:
     def adjoint(self, r: torch.Tensor, g: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         return g_adjoint(self, r, g, stream)
 
+    def tune(self, P_row: int = 0, C_col: int = 0, L_grp: int = 0, radix_order: int = -1):
+        """gj_op_tune: launch shapes and radix plan of the general product kernels."""
+        check(load().gj_op_tune(self._h, int(P_row), int(C_col), int(L_grp), int(radix_order)))
+        check(load().gj_op_info(self._h, ct.byref(self.info)))
+
+    def tiles(self) -> dict:
+        """The general kernels' current launch shapes and radix plan."""
+        return {"P_row": self.info.P_row, "C_col": self.info.C_col, "L_grp": self.info.L_grp,
+                "radix_order": self.info.radix_order}
+
     def close(self):
         if self._h is not None and self._h.value:
             load().gj_op_destroy(self._h)

@@ -28,6 +28,7 @@ struct gj_op {
     size_t spec_bytes = 0, ws_bytes = 0;
     // launch shapes
     int P_row = 8, C_col = 8, L_grp = 4;
+    int radix_order = 0;
     // 512 x 512 fast path (FP32, <= 256 prisms and stations per direction):
     // transposed spectra and intermediates, layer-sum partials and counters
     bool fast = false;
@@ -48,7 +49,7 @@ namespace gj {
 
 void set_error(const std::string &msg);
 gj_status cuda_fail(cudaError_t e, const char *what);
-bool plan_size(int N, FftPlanDev &plan);   // false if N has an unsupported factor
+bool plan_size(int N, FftPlanDev &plan, int order = 0);  // false if N has an unsupported factor
 int  autotune_size(int minN);               // smallest 7-smooth N >= minN
 size_t elem_bytes(gj_precision p);           // bytes of one real value
 void make_twiddles(int N, std::vector<double> &re, std::vector<double> &im);

@@ -650,6 +650,7 @@ struct gj_rrcg {
     std::vector<cudaGraphExec_t> seg_exec;
     cudaStream_t cap_stream = nullptr;   // stream being captured while segmenting
     cudaError_t cap_err = cudaSuccess;
+    int grid = 0;  // CTAs of the persistent fast-path launches (0: the operator's, one per SM)
 };
 
 namespace gj {
@@ -679,11 +680,13 @@ struct SolverLaunch {
     bool fast = false;
     FieldVecs<R> F;
     int P, C, L;
+    int grid;  // CTAs of the persistent fast-path launches
     size_t rsm, msm, csm;
     int n_rows_cells, n_rows_st;  // pairs in the cell / station row passes
 
     void setup() {  // views and launch shapes only (no CUDA calls: safe during capture)
         const gj_op *o = sv->op[0];
+        grid = sv->grid > 0 ? sv->grid : o->col_grid;
         v0 = view_of<R>(sv->op[0]);
         v1 = view_of<R>(sv->op[1]);
         if constexpr (std::is_same_v<R, float>) {
@@ -762,7 +765,7 @@ struct SolverLaunch {
                 pp = take_pair(sv);
                 cudaEventRecord(pp.a, st);
             }
-            f512::col_fwd<R>(V2, o->col_grid, &sv->S->done, st);
+            f512::col_fwd<R>(V2, grid, &sv->S->done, st);
             if (sv->profile && sv->capturing) {
                 cut_segment(sv, st);
             } else if (sv->profile) {
@@ -795,10 +798,10 @@ struct SolverLaunch {
             using namespace f512;
             if (opt_rows()) {
                 ProModel<R, true> pm{F, sv->S, o->nx, o->ny};
-                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
+                row_fwd_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, pm, done, st);
             } else {
                 ProModel<R, false> pm{F, sv->S, o->nx, o->ny};
-                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pm, done, st);
+                row_fwd_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, pm, done, st);
             }
             forward_columns(st);
             // residual, Phi and the residual rows' spectra for the adjoint, in one pass
@@ -822,17 +825,17 @@ struct SolverLaunch {
         const int *done = &sv->S->done;
         if constexpr (std::is_same_v<R, float>) if (fast) {
             using namespace f512;
-            col_adj<R>(V2, o->col_grid, done, st);
+            col_adj<R>(V2, grid, done, st);
             if (opt_rows()) {
                 EpiGradient<R, true> eg{F, sv->S, o->nx, o->ny};
-                row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
+                row_inv_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, eg, done, st);
                 ProDirection<R, true> pd{F, sv->S, o->nx, o->ny};
-                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
+                row_fwd_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, pd, done, st);
             } else {
                 EpiGradient<R, false> eg{F, sv->S, o->nx, o->ny};
-                row_inv_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, eg, done, st);
+                row_inv_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, eg, done, st);
                 ProDirection<R, false> pd{F, sv->S, o->nx, o->ny};
-                row_fwd_t<R>(V2, o->col_grid, o->nz, o->ny, o->nx, 0, pd, done, st);
+                row_fwd_t<R>(V2, grid, o->nz, o->ny, o->nx, 0, pd, done, st);
             }
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
@@ -1197,6 +1200,29 @@ extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj
     gj_rrcg_batch *b = new (std::nothrow) gj_rrcg_batch();
     if (!b) { set_error("gj_rrcg_batch_create: host allocation failed"); return GJ_ERR_OOM; }
     b->sv.assign(solvers, solvers + count);
+    // The branches run concurrently: the fast-path solvers share the SMs in proportion
+    // to their work (column items plus row lines per layer), so that their persistent
+    // kernels (one CTA per SM each) can be resident at the same time.  A smaller grid
+    // never needs more layer-sum slots than the operator holds (each warp's segment
+    // only grows); the check below keeps the full grid otherwise.
+    {
+        double tot = 0.0;
+        int sms = 0;
+        for (gj_rrcg *sv : b->sv)
+            if (sv->op[0]->fast && sv->prec == GJ_FP32_MIXED) {
+                tot += (double)sv->op[0]->nz * (2.0 * 257 + sv->op[0]->ny);
+                sms = sv->op[0]->col_grid;
+            }
+        for (gj_rrcg *sv : b->sv) {
+            sv->grid = 0;
+            const gj_op *o = sv->op[0];
+            if (!(o->fast && sv->prec == GJ_FP32_MIXED) || tot <= 0.0) continue;
+            const double share = (double)o->nz * (2.0 * 257 + o->ny) / tot;
+            const int g = std::max(1, (int)(sms * share));
+            if (g < o->col_grid && fast_slots(2, o->nz, g) <= o->slots && fast_slots(1, o->nz, g) <= o->slots)
+                sv->grid = g;
+        }
+    }
     // streams and events exist before the capture begins
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> br(count, nullptr);
@@ -1225,6 +1251,7 @@ extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj
         e = ce != cudaSuccess ? ce : ee;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    for (gj_rrcg *sv : b->sv) sv->grid = 0;  // stepwise calls outside the batch use the full grid
     for (int i = 0; i < count; ++i) {
         if (br[i]) cudaStreamDestroy(br[i]);
         if (join[i]) cudaEventDestroy(join[i]);

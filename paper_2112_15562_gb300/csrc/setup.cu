@@ -136,20 +136,31 @@ __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const doubl
 // ---------------------------------------------------------------------------
 // Host helpers
 
-bool plan_size(int N, FftPlanDev &plan) {
-    if (N < 1 || N > 2048) return false;
+// Radix plan of an N-point transform.  order 0: the power-of-two part in radix 8
+// (one or two radix-4 stages for the rest), then the odd primes ascending; order 1:
+// the same stages in reverse; order 2: the power-of-two part in radix 4 (and one
+// radix 2), then the odd primes.
+bool plan_size(int N, FftPlanDev &plan, int order) {
+    if (N < 1 || N > 2048 || order < 0 || order > 2) return false;
     int n = N, e = 0;
     while (n % 2 == 0) { n /= 2; ++e; }
-    std::vector<int> rs(e / 3, 8);
-    if (e % 3 == 1) {
-        if (!rs.empty()) { rs.back() = 4; rs.push_back(4); } else rs.push_back(2);
-    } else if (e % 3 == 2) {
-        rs.push_back(4);
+    std::vector<int> rs;
+    if (order == 2) {
+        rs.assign(e / 2, 4);
+        if (e % 2) rs.push_back(2);
+    } else {
+        rs.assign(e / 3, 8);
+        if (e % 3 == 1) {
+            if (!rs.empty()) { rs.back() = 4; rs.push_back(4); } else rs.push_back(2);
+        } else if (e % 3 == 2) {
+            rs.push_back(4);
+        }
     }
     const int primes[] = {3, 5, 7, 11, 13, 17};
     for (int p : primes)
         while (n % p == 0) { n /= p; rs.push_back(p); }
     if (n != 1) return false;
+    if (order == 1) std::reverse(rs.begin(), rs.end());
     if ((int)rs.size() > kMaxStages) return false;
     plan.N = N;
     plan.nst = (int)rs.size();
@@ -498,6 +509,33 @@ extern "C" gj_status gj_bttb_setup(const gj_grid *grid, gj_field field, const gj
     return gj_bttb_setup_ex(grid, field, mag, prec, Npad_y, Npad_x, 0, stream, out);
 }
 
+extern "C" gj_status gj_op_tune(gj_op *op, int P_row, int C_col, int L_grp, int radix_order) {
+    if (!op) { set_error("gj_op_tune: NULL operator"); return GJ_ERR_ARG; }
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t cs = 2 * elem_bytes(op->prec);
+    const size_t room = (size_t)optin - 1024;  // the kernels' static reduction scratch
+    if (P_row > 0 && (P_row > 64 || row_smem(op->Nx, P_row, cs) > room)) {
+        set_error("gj_op_tune: P_row too large for shared memory"); return GJ_ERR_ARG;
+    }
+    if (C_col > 0 && (C_col > 64 || col_smem(op->Ny, C_col, 3, cs) > room)) {
+        set_error("gj_op_tune: C_col too large for shared memory"); return GJ_ERR_ARG;
+    }
+    if (L_grp > 0 && L_grp > op->nz) { set_error("gj_op_tune: L_grp above nz"); return GJ_ERR_ARG; }
+    FftPlanDev px = op->px, py = op->py;
+    if (radix_order >= 0 && (!plan_size(op->Nx, px, radix_order) || !plan_size(op->Ny, py, radix_order))) {
+        set_error("gj_op_tune: radix_order must be 0, 1 or 2"); return GJ_ERR_ARG;
+    }
+    if (P_row > 0) op->P_row = P_row;
+    if (C_col > 0) op->C_col = C_col;
+    if (L_grp > 0) op->L_grp = L_grp;
+    if (radix_order >= 0) op->radix_order = radix_order;
+    op->px = px;
+    op->py = py;
+    return GJ_OK;
+}
+
 extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {
     if (!op || !info) { set_error("gj_op_info: NULL argument"); return GJ_ERR_ARG; }
     info->sx = op->sx; info->sy = op->sy; info->nx = op->nx; info->ny = op->ny; info->nz = op->nz;
@@ -506,6 +544,9 @@ extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {
     info->spectrum_bytes = (int64_t)op->spec_bytes;
     info->workspace_bytes = (int64_t)op->ws_bytes;
     info->fast_path = op->fast ? 1 : 0;
+    info->P_row = op->P_row; info->C_col = op->C_col; info->L_grp = op->L_grp;
+    info->radix_order = op->radix_order;
+    info->recompute = op->recompute ? 1 : 0;
     return GJ_OK;
 }
 

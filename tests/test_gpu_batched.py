@@ -66,6 +66,76 @@ def test_batched_graph_equals_one_by_one():
             assert rel(a[i], b[i]) <= 1e-5
 
 
+def test_batched_problem_matches_oracle():
+    """One problem of a batch (16x16x6 on the 512 kernels, data from the dense oracle)
+    against the FP64 oracle's RRCG, while two other problems of different sizes run in
+    the same graph (Eq. RRCG:1-8); the batch gives each fast-path solver a share of
+    the SMs, so the branches run concurrently."""
+    from oracle import operator as oop
+    from oracle.rrcg import RRCGParams, rrcg_joint
+
+    gj = lib()
+    g = synth.uniform_grid(16, 16, 16, 16, 6, 50.0)
+    mag = synth.Mag(50000.0, 60.0, 10.0)
+    A = [oop.dense_matrix(g, oop.GRAVITY), oop.dense_matrix(g, oop.MAGNETIC, mag)]
+    mt = [synth.dipping_blocks(g, v, 91, count=2) for v in (1.0, 0.1)]
+    e = synth.standard_normal((2, g.s), 92)
+    obs = [owt.noisy_data(A[i] @ mt[i], 0.01, 0.01, e[i]) for i in range(2)]
+    dob, sig = [o[0] for o in obs], [o[1] for o in obs]
+    wdep = [owt.depth_weights(g.z_edges, b) for b in (2.0, 3.0)]
+    kw = dict(p=(1, 1), lam=(2.0, 100.0), kmax=12, stop_on_chi2=False)
+    ref = rrcg_joint([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
+                     dob, sig, [np.zeros(g.n)] * 2, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)],
+                     RRCGParams(**kw))
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).float().cuda()
+    ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512)),
+           gj.bttb_setup(g, "magnetic", mag, precision="fp32", npad=(512, 512))]
+    m = [torch.zeros(g.n, device="cuda") for _ in range(2)]
+    solvers = [gj.Solver(ops, gj.solver_params(**kw), [dev(x) for x in dob], [dev(x) for x in sig],
+                         [dev(x) for x in wdep], m, history=True)]
+    others = []
+    for i, (nx, ny, nz) in enumerate([(24, 20, 5), (40, 40, 8)]):
+        go, opso, dobo, sigo, wdo = make_problem(gj, nx, ny, nz, 60 + i, npad=(512, 512))
+        mo = [torch.zeros(go.n, device="cuda") for _ in range(2)]
+        others.append((opso, dobo, sigo, wdo, mo))
+        solvers.append(gj.Solver(opso, gj.solver_params(**kw), dobo, sigo, wdo, mo))
+    b = gj.Batch(solvers)
+    b.step(12)
+    torch.cuda.synchronize()
+    b.close()
+    rep = solvers[0].report()
+    assert rep["iterations"] == 12
+    for k in range(13):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-4), (k, i)
+    for i in range(2):
+        assert rel(m[i].double().cpu().numpy(), ref.m[i]) <= 1e-3
+    for s_ in solvers:
+        s_.close()
+
+
+def test_op_tune_keeps_the_product():
+    """gj_op_tune (tiles and radix plan of the general kernels) changes only rounding."""
+    gj = lib()
+    g = synth.uniform_grid(20, 18, 20, 18, 4, 50.0)
+    from oracle import operator as oop
+
+    A = oop.dense_matrix(g, oop.MAGNETIC, synth.Mag(50000.0, 60.0, 10.0))
+    op = gj.bttb_setup(g, "magnetic", synth.Mag(50000.0, 60.0, 10.0), precision="fp64", npad=(40, 42))
+    m = np.random.default_rng(1).standard_normal(g.n)
+    for kw in ({}, {"P_row": 2}, {"C_col": 1}, {"L_grp": 1}, {"radix_order": 1}, {"radix_order": 2},
+               {"P_row": 16, "C_col": 16, "L_grp": 4, "radix_order": 0}):
+        op.tune(**kw)
+        for k, v in kw.items():
+            assert op.tiles()[k] == v
+        d = op.forward(torch.from_numpy(m).cuda()).cpu().numpy()
+        assert rel(d, A @ m) <= 1e-10, kw
+    with pytest.raises(gj.GJError):
+        op.tune(P_row=4096)
+    with pytest.raises(gj.GJError):
+        op.tune(radix_order=7)
+
+
 def test_autotuner_picks_a_valid_size_and_caches(tmp_path):
     gj = lib()
     from paper_2112_15562_gb300 import autotune
@@ -81,6 +151,13 @@ def test_autotuner_picks_a_valid_size_and_caches(tmp_path):
     assert "512x512" in entry["ms_fwd_adj_both_fields"]
     assert autotune.tune(g, mag, "fp32", cache=cache) == npad  # served from the cache
     assert autotune.smooth_sizes(511, 3) == [512, 525, 540]
+    # the full search on FP64 (general kernels only): size, radix plan and tiles
+    npad64, tiles = autotune.tune_full(g, mag, "fp64", cache=cache, reps=2)
+    assert npad64[0] >= 79 and npad64[1] >= 79
+    assert set(tiles) <= set(autotune.KNOBS) and all(v in autotune.KNOBS[k] for k, v in tiles.items())
+    entry = json.load(open(cache))[autotune._key(g, "fp64")]
+    assert any(k.endswith("tuned") for k in entry["ms_fwd_adj_both_fields"])
+    assert autotune.tune_full(g, mag, "fp64", cache=cache) == (npad64, tiles)
 
 
 def test_lambda_sweep_matches_single_solves():

@@ -3,8 +3,7 @@ workload on a 1024 x 1024 embedding (Sec. 2.7.1, Eq. d=gm).
 
 * Small grids: products of operators that rebuild each layer's spectrum before use
   equal the dense FP64 oracle within the usual tolerances and equal the stored-spectra
-  operators (the spectra are bit-identical; the forward's layer sums may round in
-  another order).
+  operators to rounding (the same FP64 build, one layer at a time).
 * 512x512 stations over 512x512x48 cells of 100 m (12.6 M cells per model), FP32,
   padded 1024 x 1024: sampled forward rows and adjoint cells of both fields, with
   stored and with recomputed spectra, against the oracle's dense rows and columns
@@ -26,7 +25,7 @@ MAG = synth.Mag(50000.0, 60.0, 10.0)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("npad", [(0, 0), (25, 21)])
+@pytest.mark.parametrize("npad", [(0, 0), (21, 25)])
 def test_recompute_matches_stored_and_oracle(prec, npad):
     gj = lib()
     g = synth.uniform_grid(12, 10, 12, 10, 5, 40.0)
@@ -42,8 +41,11 @@ def test_recompute_matches_stored_and_oracle(prec, npad):
         d_s, d_r = st.forward(to_dev(m, prec)).cpu().numpy(), rc.forward(to_dev(m, prec)).cpu().numpy()
         a_s, a_r = st.adjoint(to_dev(r, prec)).cpu().numpy(), rc.adjoint(to_dev(r, prec)).cpu().numpy()
         assert rel(d_r, A @ m) <= TOL[prec] and rel(a_r, A.T @ r) <= TOL[prec]
-        assert np.array_equal(a_r, a_s)  # per-layer products from identical spectra
-        assert rel(d_r, d_s) <= (1e-13 if prec == "fp64" else 1e-6)
+        # the same FP64 build, one layer at a time: with an odd padded size the setup's
+        # row transforms pair lines across layers differently, so the spectra agree to
+        # rounding; the forward's layer sums also round in another order
+        tol = 1e-13 if prec == "fp64" else 1e-6
+        assert rel(a_r, a_s) <= tol and rel(d_r, d_s) <= tol
 
 
 def test_recompute_operator_is_rejected_by_the_solver():
@@ -97,6 +99,6 @@ def test_512x48_on_a_1024_embedding_sampled():
             print(f"\n512x512x48 N=1024 {field} {mode}: sampled forward rel {ed:.2e}, sampled adjoint rel {ea:.2e}")
             assert ed <= TOL["fp32"] and ea <= TOL["fp32"], (field, mode, ed, ea)
             out[mode] = (d, a)
-        assert np.array_equal(out["stored"][1], out["recomputed"][1])
+        assert rel(out["recomputed"][1], out["stored"][1]) <= 1e-6
         assert rel(out["recomputed"][0], out["stored"][0]) <= 1e-6
         torch.cuda.empty_cache()
