@@ -20,18 +20,39 @@ from __future__ import annotations
 
 import numpy as np
 
-from .prism import prism_dT, prism_gz
+from .prism import FAR, prism_dT, prism_dT_cubature, prism_gz, prism_gz_cubature
 
 GRAVITY = 1
 MAGNETIC = 2
 
 
 def _kernel(field, mag, x0, y0, z0, x1, x2, y1, y2, z1, z2):
+    """The prism field for broadcast arrays of stations and prisms: the closed form
+    (corner sums) near the station, cubature for prisms whose centre is at least FAR
+    times their largest side away (where the corner sums cancel)."""
+    if field not in (GRAVITY, MAGNETIC):
+        raise ValueError(field)
+    a = np.broadcast_arrays(*[np.asarray(v, dtype=np.float64) for v in (x0, y0, z0, x1, x2, y1, y2, z1, z2)])
+    x0, y0, z0, x1, x2, y1, y2, z1, z2 = [v.reshape(-1) for v in a]
+    size = np.maximum(np.maximum(x2 - x1, y2 - y1), z2 - z1)
+    dist = np.sqrt((0.5 * (x1 + x2) - x0) ** 2 + (0.5 * (y1 + y2) - y0) ** 2 + (0.5 * (z1 + z2) - z0) ** 2)
+    out = np.empty(x0.shape)
+    near = dist < FAR * size
+    args = lambda m: (x0[m], y0[m], z0[m], x1[m], x2[m], y1[m], y2[m], z1[m], z2[m])
     if field == GRAVITY:
-        return prism_gz(x0, y0, z0, x1, x2, y1, y2, z1, z2)
-    if field == MAGNETIC:
-        return prism_dT(x0, y0, z0, x1, x2, y1, y2, z1, z2, mag.F, mag.incl, mag.decl)
-    raise ValueError(field)
+        out[near] = prism_gz(*args(near))
+    else:
+        out[near] = prism_dT(*args(near), mag.F, mag.incl, mag.decl)
+    order = np.where(near, 0, np.where(dist < 2.0 * FAR * size, 5, 4))  # prism.cubature_order
+    for n in (5, 4):
+        m = order == n
+        if not m.any():
+            continue
+        if field == GRAVITY:
+            out[m] = prism_gz_cubature(*args(m), n=n)
+        else:
+            out[m] = prism_dT_cubature(*args(m), mag.F, mag.incl, mag.decl, n=n)
+    return out.reshape(a[0].shape)
 
 
 def station_xy(grid):

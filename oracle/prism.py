@@ -11,6 +11,14 @@ R = sqrt(u^2 + v^2 + w^2).  The definite triple integral of a mixed third
 derivative f_uvw is the corner sum  sum_{i,j,k in {1,2}} (-1)^(i+j+k) f(u_i, v_j, w_k)
 with index 2 the upper limit.
 
+Far from the station the corner sum cancels: its eight terms grow like R log R
+while the field falls like 1 / R^2, and at 100 cell sizes the FP64 sum keeps only
+about 7 digits.  There the same integrals are evaluated by tensor Gauss-Legendre
+cubature of the smooth integrands (``prism_gz_cubature``, ``prism_dT_cubature``),
+which is accurate to about 1e-13 from 8 cell sizes out; ``oracle.operator`` picks
+the cubature for prisms whose centre is at least ``FAR`` times their largest side
+from the station.
+
 Station placement: stations sit at or above the prism tops (w >= 0 at every
 corner).  On a top face (w = 0) the arctangent terms take their limit from the
 air side, atan2(., +0) = +-pi/2, which keeps the field continuous as the station
@@ -111,3 +119,51 @@ def prism_dT(x0, y0, z0, x1, x2, y1, y2, z1, z2, F, incl, decl):
     q = (t[0] * t[0] * hxx + t[1] * t[1] * hyy + t[2] * t[2] * hzz
          + 2.0 * (t[0] * t[1] * hxy + t[0] * t[2] * hxz + t[1] * t[2] * hyz))
     return F / (4.0 * np.pi) * q
+
+
+# prisms at least FAR times their largest side away are integrated by cubature
+FAR = 8.0
+
+
+def _gauss_box(x0, y0, z0, x1, x2, y1, y2, z1, z2, n, integrand):
+    """Tensor n-point Gauss-Legendre rule of integrand(u, v, w) over the prism, for
+    arrays of prisms (broadcast); u, v, w are source minus station coordinates."""
+    x, wt = np.polynomial.legendre.leggauss(n)
+    arrs = np.broadcast_arrays(*[np.asarray(a, dtype=np.float64) for a in (x0, y0, z0, x1, x2, y1, y2, z1, z2)])
+    x0, y0, z0, x1, x2, y1, y2, z1, z2 = [a[..., None] for a in arrs]
+    cu, hu = 0.5 * (x1 + x2) - x0, 0.5 * (x2 - x1)
+    cv, hv = 0.5 * (y1 + y2) - y0, 0.5 * (y2 - y1)
+    cw, hw = 0.5 * (z1 + z2) - z0, 0.5 * (z2 - z1)
+    total = 0.0
+    for i in range(n):
+        u = cu + hu * x[i]
+        for j in range(n):
+            v = cv + hv * x[j]
+            w = cw + hw * x  # all n nodes in w at once (last axis)
+            total = total + wt[i] * wt[j] * np.sum(wt * integrand(u, v, w), axis=-1, keepdims=True)
+    return (total * hu * hv * hw)[..., 0]
+
+
+def prism_gz_cubature(x0, y0, z0, x1, x2, y1, y2, z1, z2, n=5):
+    """Vertical gravity (mGal per g/cc) by cubature of G w / R^3."""
+    def f(u, v, w):
+        r2 = u * u + v * v + w * w
+        return w / (r2 * np.sqrt(r2))
+    return GRAV_UNIT * _gauss_box(x0, y0, z0, x1, x2, y1, y2, z1, z2, n, f)
+
+
+def prism_dT_cubature(x0, y0, z0, x1, x2, y1, y2, z1, z2, F, incl, decl, n=5):
+    """Total-field anomaly (nT per SI) by cubature of (F / 4 pi) t^T (d2 (1/R) / dr dr) t,
+    where t^T (d2 (1/R)) t = (3 (t . r)^2 - R^2) / R^5 for the unit vector t."""
+    t = inducing_direction(incl, decl)
+
+    def f(u, v, w):
+        r2 = u * u + v * v + w * w
+        tr = t[0] * u + t[1] * v + t[2] * w
+        return (3.0 * tr * tr - r2) / (r2 * r2 * np.sqrt(r2))
+    return F / (4.0 * np.pi) * _gauss_box(x0, y0, z0, x1, x2, y1, y2, z1, z2, n, f)
+
+
+def cubature_order(distance, size):
+    """Points per axis of the far-field rule: 5 from FAR to 2 FAR sizes, 4 beyond."""
+    return 5 if distance < 2.0 * FAR * size else 4

@@ -65,20 +65,93 @@ __global__ void k_corner_lattice(Lattice L, int magnetic, MagCoef mc, double *ou
     }
 }
 
+// Far from the station the 8-corner sums cancel (their terms grow like R log R
+// while the field falls like 1/R^2): a prism whose centre is at least kFar times its
+// largest side away is integrated by tensor Gauss-Legendre cubature of the smooth
+// integrand instead, 5 points per axis up to 2 kFar sides and 4 beyond (relative
+// error about 1e-13 there, against 1e-7 for the corner sums at 100 sides).
+constexpr double kFar = 8.0;
+// Gauss-Legendre nodes and weights on [-1, 1]
+__constant__ double kGL5x[5] = {-0.90617984593866399280, -0.53846931010568309104, 0.0, 0.53846931010568309104,
+                                0.90617984593866399280};
+__constant__ double kGL5w[5] = {0.23692688505618908751, 0.47862867049936646804, 0.56888888888888888889,
+                                0.47862867049936646804, 0.23692688505618908751};
+__constant__ double kGL4x[4] = {-0.86113631159405257522, -0.33998104358485626480, 0.33998104358485626480,
+                                0.86113631159405257522};
+__constant__ double kGL4w[4] = {0.34785484513745385737, 0.65214515486254614263, 0.65214515486254614263,
+                                0.34785484513745385737};
+
+// The integral over [u1, u2] x [v1, v2] x [w1, w2] of w / R^3 (gravity) or of
+// t^T (d2(1/R)/dr dr) t = (c0 (3u^2 - R^2) + c1 (3v^2 - R^2) + c2 (3w^2 - R^2)
+// + 3 (c3 uv + c4 uw + c5 vw)) / R^5 (magnetic), by an n-point tensor rule.
+template <int NP>
+__device__ double far_cubature(double uc, double hu, double vc, double hv, double wc, double hw, int magnetic,
+                               const MagCoef &k) {
+    const double *x = NP == 5 ? kGL5x : kGL4x;
+    const double *wt = NP == 5 ? kGL5w : kGL4w;
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+        const double u = uc + hu * x[a];
+#pragma unroll
+        for (int b = 0; b < NP; ++b) {
+            const double v = vc + hv * x[b];
+            double sw = 0.0;
+#pragma unroll
+            for (int c = 0; c < NP; ++c) {
+                const double w = wc + hw * x[c];
+                const double r2 = u * u + v * v + w * w;
+                const double ir = rsqrt(r2);
+                const double ir3 = ir * ir * ir;
+                double f;
+                if (magnetic) {
+                    const double q = k.c[0] * (3.0 * u * u - r2) + k.c[1] * (3.0 * v * v - r2) +
+                                     k.c[2] * (3.0 * w * w - r2) + 3.0 * (k.c[3] * u * v + k.c[4] * u * w + k.c[5] * v * w);
+                    f = q * ir3 * ir * ir;
+                } else {
+                    f = w * ir3;
+                }
+                sw += wt[c] * f;
+            }
+            s += wt[a] * wt[b] * sw;
+        }
+    }
+    return s * hu * hv * hw;
+}
+
 // Row-pass input of the setup: the circulant embedding of layer r's table,
 // T[c_y mod Ny][c_x mod Nx] = K(c_y + off_y, c_x + off_x) for c in
-// [-(n-1), s-1], zero elsewhere; K is the 8-corner sum of the lattice.
+// [-(n-1), s-1], zero elsewhere; K is the 8-corner sum of the lattice, or the
+// far-field cubature.
 struct LoadTable {
     const double *lat;
     int nbx1, nby1;
     int Nx, Ny, sx, sy, nx, ny, off_x, off_y, a_max, b_max;
     double scale;
+    double dx, dy;
+    const double *zw;  // depth planes of the build's layers (relative to the stations)
+    int magnetic;
+    MagCoef mc;
     __device__ void init() {}
     __device__ double value(int line, int j) const {
         const int r = line / Ny, iy = line % Ny;
         int cy, cx;
         if (iy <= sy - 1) cy = iy; else if (iy >= Ny - (ny - 1)) cy = iy - Ny; else return 0.0;
         if (j <= sx - 1) cx = j; else if (j >= Nx - (nx - 1)) cx = j - Nx; else return 0.0;
+        {
+            // the prism spans u in [-(cx + off_x) -+ 1/2] dx, v likewise, w in [zw[r], zw[r + 1]]
+            const double uc = -(double)(cx + off_x) * dx, vc = -(double)(cy + off_y) * dy;
+            const double w1 = zw[r], w2 = zw[r + 1];
+            const double wc = 0.5 * (w1 + w2), hw = 0.5 * (w2 - w1);
+            const double size = fmax(fmax(dx, dy), w2 - w1);
+            const double dist = sqrt(uc * uc + vc * vc + wc * wc);
+            if (dist >= kFar * size) {
+                const double v = dist < 2.0 * kFar * size
+                                     ? far_cubature<5>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
+                                     : far_cubature<4>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc);
+                return v * scale;
+            }
+        }
         const int e = b_max - (cx + off_x);
         const int f = a_max - (cy + off_y);
         double s = 0.0;
@@ -347,6 +420,10 @@ static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r
     lt.Nx = op->Nx; lt.Ny = op->Ny; lt.sx = op->sx; lt.sy = op->sy; lt.nx = op->nx; lt.ny = op->ny;
     lt.off_x = op->off_x; lt.off_y = op->off_y; lt.a_max = L.a_max; lt.b_max = L.b_max;
     lt.scale = scale;
+    lt.dx = op->dx; lt.dy = op->dy;
+    lt.zw = sc.zw + r0;
+    lt.magnetic = magnetic;
+    lt.mc = mc;
     PairMap pm{count * op->Ny, 0};
     const int P = pick_row_pairs(op->Nx, sizeof(double2));
     const int npairs = (pm.nlines + 1) / 2;

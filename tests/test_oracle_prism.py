@@ -118,3 +118,77 @@ def test_vertical_inclination_reduces_to_hzz():
     t = prism.inducing_direction(60.0, 10.0)
     assert np.linalg.norm(t) == pytest.approx(1.0)
     assert t[2] > 0 and t[1] > t[0] > 0  # down, mostly north, a little east
+
+
+# ---------------------------------------------------------------------------
+# Far-field cubature (used for prisms at least FAR sizes from the station, where
+# the corner sums cancel)
+
+def _box(off, h=100.0, dz=100.0):
+    ox, oy, oz = off
+    return ((ox - 0.5) * h, (ox + 0.5) * h, (oy - 0.5) * h, (oy + 0.5) * h, (oz - 0.5) * dz, (oz + 0.5) * dz)
+
+
+@pytest.mark.parametrize("off", [(8.0, 0.0, 1.5), (5.0, 6.0, 2.5), (6.0, 6.0, 4.0), (1.5, 2.5, 9.0)])
+def test_cubature_equals_closed_form_where_both_hold(off):
+    """8-12 sizes out the corner sums still keep about 11 digits: both evaluations of
+    the Sec. 2.1 integrals agree to 1e-10."""
+    x1, x2, y1, y2, z1, z2 = _box(off)
+    g_c = prism.prism_gz(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2)
+    g_q = prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2)
+    assert g_q == pytest.approx(g_c, rel=1e-10)
+    m_c = prism.prism_dT(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 50000.0, 60.0, 10.0)
+    m_q = prism.prism_dT_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 50000.0, 60.0, 10.0)
+    assert m_q == pytest.approx(m_c, rel=1e-10)
+
+
+@pytest.mark.parametrize("off", [(20.0, 7.0, 3.5), (60.0, 60.0, 30.5), (150.0, 90.0, 12.5)])
+def test_cubature_converges_far_out(off):
+    x1, x2, y1, y2, z1, z2 = _box(off)
+    for n_lo, n_hi in ((4, 6), (5, 7)):
+        a = prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, n=n_lo)
+        b = prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, n=n_hi)
+        assert a == pytest.approx(b, rel=2e-13)
+        a = prism.prism_dT_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 5e4, 60.0, 10.0, n=n_lo)
+        b = prism.prism_dT_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 5e4, 60.0, 10.0, n=n_hi)
+        assert a == pytest.approx(b, rel=2e-13)
+    # and tends to the point mass: G rho V w / R^3 (mGal per g/cc)
+    d = np.array([0.5 * (x1 + x2), 0.5 * (y1 + y2), 0.5 * (z1 + z2)])
+    R = np.linalg.norm(d)
+    pm = prism.GRAV_UNIT * (x2 - x1) * (y2 - y1) * (z2 - z1) * d[2] / R ** 3
+    assert prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2) == pytest.approx(pm, rel=3.0 / (R / 100.0) ** 2)
+
+
+def test_cubature_hessian_trace_vanishes():
+    """Laplace: the three axis-aligned inducing directions sum to the trace of the
+    Hessian of 1/R, zero away from the source."""
+    x1, x2, y1, y2, z1, z2 = _box((30.0, 11.0, 6.5))
+    s = sum(prism.prism_dT_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 4 * np.pi, inc, dec)
+            for inc, dec in ((0.0, 90.0), (0.0, 0.0), (90.0, 0.0)))
+    scale = abs(prism.prism_dT_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, 4 * np.pi, 90.0, 0.0))
+    assert abs(s) <= 1e-12 * scale
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).nmant < 63, reason="needs extended precision")
+def test_cubature_against_extended_precision_corner_sums():
+    """Far out the FP64 corner sums lose digits (the eight terms are ~1e6 times the
+    field); in extended precision they keep about 12, and the cubature matches them."""
+    L = np.longdouble
+
+    def gz_ld(x1, x2, y1, y2, z1, z2):
+        def f(u, v, w):
+            u, v, w = L(u), L(v), L(w)
+            R = np.sqrt(u * u + v * v + w * w)
+            lg = lambda a, b, c: np.log(a + R) if a >= 0 else np.log((b * b + c * c) / (R - a))
+            return -(u * lg(v, u, w) + v * lg(u, v, w) - w * np.arctan2(u * v, w * R))
+        s = L(0)
+        for i, u in ((1, x1), (2, x2)):
+            for j, v in ((1, y1), (2, y2)):
+                for k, w in ((1, z1), (2, z2)):
+                    s += (-1) ** (i + j + k) * f(u, v, w)
+        return float(s * L(prism.GRAV_UNIT))
+
+    for off in [(40.0, 40.0, 20.5), (24.0, 3.0, 10.5)]:
+        x1, x2, y1, y2, z1, z2 = _box(off)
+        ref = gz_ld(x1, x2, y1, y2, z1, z2)
+        assert prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2) == pytest.approx(ref, rel=1e-11)
