@@ -233,6 +233,17 @@ gj_status gj_gramian_value_grad_noalloc(int64_t n, gj_precision precision,
                                         const void *m1, const void *m2, double *S,
                                         void *l1, void *l2, gj_stream_t stream);
 
+/*
+ * gj_pearson - Pearson correlation coefficient of the vectors a and b (n values
+ * each, the given precision) into the device double *r: means first, then the
+ * centred sums in FP64 (0 when either vector has no spread).  The measure of
+ * "correlated models" in the lambda selection of Secs. 3.1.3 and 5, whose
+ * figures judge it from density-susceptibility cross-plots.  Asynchronous on
+ * `stream`; allocates its reduction scratch with cudaMallocAsync.
+ */
+gj_status gj_pearson(int64_t n, gj_precision precision, const void *a, const void *b, double *r,
+                     gj_stream_t stream);
+
 /* Solver options (Eq. RRCG:1-8; Secs. 2.5, 2.6, 2.8). Index 0 = gravity, 1 = magnetic. */
 enum { GJ_SCALARS_AUTO = 0, GJ_SCALARS_JOINT = 1, GJ_SCALARS_PER_FIELD = 2 };
 /* Regulariser anchor of RRCG:4: the a-priori model W_k m_apr (default; the first
@@ -327,6 +338,9 @@ gj_status gj_rrcg_create(const gj_op *const ops[2], const gj_rrcg_params *params
 gj_status gj_rrcg_iterate(gj_rrcg *solver, int iters, int use_graph, gj_stream_t stream);
 /* Synchronises `stream` and fills *rep (host). */
 gj_status gj_rrcg_report_get(gj_rrcg *solver, gj_rrcg_report *rep, gj_stream_t stream);
+/* Writes the same report into DEVICE memory `rep` (one thread, asynchronous on
+ * `stream`, no host round trip), e.g. from inside a captured loop. */
+gj_status gj_rrcg_report_device(gj_rrcg *solver, gj_rrcg_report *rep, gj_stream_t stream);
 /* Synchronises `stream`; returns 1 once the device-side stop flag is set, 0 if
  * not, -1 on error. */
 int gj_rrcg_done(gj_rrcg *solver, gj_stream_t stream);

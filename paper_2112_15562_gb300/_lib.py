@@ -93,6 +93,8 @@ def load() -> ct.CDLL:
         "gj_rrcg_iterate": (i32, [vp, i32, i32, vp]),
         "gj_rrcg_report_get": (i32, [vp, ct.POINTER(RRCGReport), vp]),
         "gj_rrcg_done": (i32, [vp, vp]),
+        "gj_rrcg_report_device": (i32, [vp, vp, vp]),
+        "gj_pearson": (i32, [i64, i32, vp, vp, vp, vp]),
         "gj_rrcg_profile": (i32, [vp, i32]),
         "gj_rrcg_profile_read": (i32, [vp, ct.POINTER(i32), ct.POINTER(d)]),
         "gj_rrcg_destroy": (None, [vp]),

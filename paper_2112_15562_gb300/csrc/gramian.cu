@@ -85,6 +85,71 @@ static gj_status gramian_launch(int64_t n, const void *m1, const void *m2, doubl
 
 }  // namespace gj
 
+// Pearson coefficient of two vectors: means in a first pass, centred sums in a
+// second (FP64 accumulation), the ratio in one thread.
+namespace gj {
+template <typename R>
+__global__ void __launch_bounds__(256) k_sums2(int64_t n, const R *a, const R *b, double *part) {
+    __shared__ double red[32];
+    double sa = 0, sb = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        sa += (double)a[i];
+        sb += (double)b[i];
+    }
+    sa = block_sum(sa, red);
+    sb = block_sum(sb, red);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = sa; part[2 * blockIdx.x + 1] = sb; }
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_centred3(int64_t n, const R *a, const R *b, const double *part, int nb,
+                                                  double *part2) {
+    __shared__ double red[32];
+    __shared__ double mean[2];
+    if (threadIdx.x < 2) {
+        double t = 0;
+        for (int k = 0; k < nb; ++k) t += part[2 * k + threadIdx.x];
+        mean[threadIdx.x] = t / (double)n;
+    }
+    __syncthreads();
+    const double ma = mean[0], mb = mean[1];
+    double saa = 0, sbb = 0, sab = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)a[i] - ma, y = (double)b[i] - mb;
+        saa += x * x; sbb += y * y; sab += x * y;
+    }
+    saa = block_sum(saa, red);
+    sbb = block_sum(sbb, red);
+    sab = block_sum(sab, red);
+    if (threadIdx.x == 0) { part2[3 * blockIdx.x] = saa; part2[3 * blockIdx.x + 1] = sbb; part2[3 * blockIdx.x + 2] = sab; }
+}
+__global__ void k_pearson_finish(int nb, const double *part2, double *r) {
+    double saa = 0, sbb = 0, sab = 0;
+    for (int k = 0; k < nb; ++k) { saa += part2[3 * k]; sbb += part2[3 * k + 1]; sab += part2[3 * k + 2]; }
+    const double den = sqrt(saa * sbb);
+    *r = den > 0 ? sab / den : 0.0;
+}
+template <typename R>
+static gj_status pearson_launch(int64_t n, const void *a, const void *b, double *r, cudaStream_t st) {
+    const int nb = (int)std::min<int64_t>(2 * 152, std::max<int64_t>(1, (n + 255) / 256));
+    double *scratch = nullptr;
+    GJ_CUDA(cudaMallocAsync(&scratch, 5 * (size_t)nb * sizeof(double), st));
+    k_sums2<R><<<nb, 256, 0, st>>>(n, (const R *)a, (const R *)b, scratch);
+    k_centred3<R><<<nb, 256, 0, st>>>(n, (const R *)a, (const R *)b, scratch, nb, scratch + 2 * nb);
+    k_pearson_finish<<<1, 1, 0, st>>>(nb, scratch + 2 * nb, r);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? GJ_OK : cuda_fail(e, "pearson launch");
+}
+}  // namespace gj
+
+extern "C" gj_status gj_pearson(int64_t n, gj_precision prec, const void *a, const void *b, double *r,
+                                gj_stream_t stream) {
+    if (n < 1 || !a || !b || !r) { gj::set_error("gj_pearson: bad argument"); return GJ_ERR_ARG; }
+    if (prec != GJ_FP64 && prec != GJ_FP32_MIXED) { gj::set_error("gj_pearson: bad precision"); return GJ_ERR_ARG; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return prec == GJ_FP64 ? gj::pearson_launch<double>(n, a, b, r, st) : gj::pearson_launch<float>(n, a, b, r, st);
+}
+
 extern "C" gj_status gj_gramian_value_grad(int64_t n, gj_precision prec, const void *m1, const void *m2,
                                            double *S, void *l1, void *l2, gj_stream_t stream) {
     if (n < 1 || !m1 || !m2 || !S) { gj::set_error("gj_gramian_value_grad: bad argument"); return GJ_ERR_ARG; }

@@ -617,6 +617,22 @@ __global__ void k_scalars_after_direction(SolverDev *S) {
     S->k = k + 1;
 }
 
+// The report of the solver state into device memory (one thread): the same fields
+// as gj_rrcg_report_get, without a host round trip.
+__global__ void k_report(const SolverDev *S, const int *err, gj_rrcg_report *rep) {
+    rep->status = S->status;
+    if (err && *err != 0 && rep->status == GJ_OK) rep->status = *err;
+    rep->iterations = S->k;
+    rep->converged = S->sat[0] && S->sat[1];
+    rep->satisfied[0] = S->sat[0];
+    rep->satisfied[1] = S->sat[1];
+    rep->phi[0] = S->phi_last[0];
+    rep->phi[1] = S->phi_last[1];
+    rep->alpha[0] = S->alpha[0];
+    rep->alpha[1] = S->alpha[1];
+    rep->S_G = S->SG_last;
+}
+
 template <typename R>
 __global__ void k_reciprocal(int n, const R *sigma, R *wd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wd[i] = R(1) / sigma[i];
@@ -1086,6 +1102,14 @@ extern "C" gj_status gj_rrcg_report_get(gj_rrcg *sv, gj_rrcg_report *rep, gj_str
         GJ_CUDA(cudaMemcpy(&e, sv->op[0]->err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e != 0 && rep->status == GJ_OK) rep->status = e;
     }
+    return GJ_OK;
+}
+
+extern "C" gj_status gj_rrcg_report_device(gj_rrcg *sv, gj_rrcg_report *rep, gj_stream_t stream) {
+    if (!sv || !rep) { set_error("gj_rrcg_report_device: NULL argument"); return GJ_ERR_ARG; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_report<<<1, 1, 0, st>>>(sv->S, sv->op[0]->err, rep);
+    GJ_CUDA(cudaGetLastError());
     return GJ_OK;
 }
 

@@ -6,7 +6,7 @@ the density-susceptibility cross-plot) and fit both data sets.  Here every pair 
 one solver; all of them advance together in one batched CUDA graph
 (gj_rrcg_batch_*).  Each pair gets its own operators because an operator's
 workspace cannot be shared by concurrent solvers.  The correlation of the final
-models is reported as a Pearson coefficient, computed on the host.
+models is reported as a Pearson coefficient (gj_pearson, on the device).
 """
 from __future__ import annotations
 
@@ -18,11 +18,24 @@ import torch
 from .api import Batch, Solver, bttb_setup, solver_params
 
 
-def pearson(a: np.ndarray, b: np.ndarray) -> float:
-    a = np.asarray(a, dtype=np.float64) - np.mean(a)
-    b = np.asarray(b, dtype=np.float64) - np.mean(b)
-    den = np.sqrt((a @ a) * (b @ b))
-    return float(a @ b / den) if den > 0 else 0.0
+def pearson(a, b, stream=None) -> float:
+    """Pearson coefficient of two models (gj_pearson on the device; numpy arrays are
+    copied to the device first).  Returns a float."""
+    import ctypes as ct
+
+    from . import _lib
+    from .api import _ptr, _stream
+
+    ta = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+    tb = b if isinstance(b, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(b, dtype=np.float64))
+    ta = ta.cuda().contiguous()
+    tb = tb.to(device=ta.device, dtype=ta.dtype).contiguous()
+    if ta.dtype not in (torch.float32, torch.float64) or ta.numel() != tb.numel():
+        raise ValueError("pearson: two float32 or float64 vectors of one length")
+    prec = _lib.GJ_FP64 if ta.dtype == torch.float64 else _lib.GJ_FP32_MIXED
+    r = torch.empty(1, dtype=torch.float64, device=ta.device)
+    _lib.check(_lib.load().gj_pearson(ta.numel(), prec, _ptr(ta), _ptr(tb), _ptr(r), _stream(stream)))
+    return float(r.item())
 
 
 def lambda_sweep(grid, mag, dobs, sigma, w_depth, lambdas: Sequence[Tuple[float, float]], precision: str = "fp32",
@@ -47,11 +60,12 @@ def lambda_sweep(grid, mag, dobs, sigma, w_depth, lambdas: Sequence[Tuple[float,
     batch.close()
     for lam, s, (ops, m) in zip(lambdas, solvers, keep):
         rep = s.report()
+        r = pearson(m[0], m[1])
         m1 = m[0].double().cpu().numpy()
         m2 = m[1].double().cpu().numpy()
         runs.append({"lambda": [float(lam[0]), float(lam[1])], "iterations": rep["iterations"],
                      "converged": rep["converged"], "phi": rep["phi"], "S_G": rep["S_G"],
-                     "pearson": pearson(m1, m2), "models": (m1, m2)})
+                     "pearson": r, "models": (m1, m2)})
         s.close()
         for o in ops:
             o.close()

@@ -94,3 +94,28 @@ def test_op_status_of_a_healthy_fast_operator():
     assert L.gj_op_status(op.handle, 1, stream) == 0
     slow = gj.bttb_setup(g, "gravity", precision="fp64")
     assert L.gj_op_status(slow.handle, 1, stream) == 0
+
+
+def test_device_report_equals_host_report():
+    """gj_rrcg_report_device writes the report into device memory without a host round
+    trip; it must equal gj_rrcg_report_get."""
+    gj = lib()
+    from paper_2112_15562_gb300 import _lib
+
+    L = _lib.load()
+    w, g, dob, sig, wdep = small_inputs()
+    ops = [gj.bttb_setup(g, "gravity", precision="fp64"), gj.bttb_setup(g, "magnetic", w.mag, precision="fp64")]
+    m = [to_dev(np.zeros(g.n), "fp64") for _ in range(2)]
+    sv = gj.Solver(ops, gj.solver_params(p=(1, 1), lam=(50.0, 1500.0), kmax=6, stop_on_chi2=False),
+                   [to_dev(x, "fp64") for x in dob], [to_dev(x, "fp64") for x in sig],
+                   [to_dev(x, "fp64") for x in wdep], m)
+    sv.iterate(4)
+    buf = torch.zeros(ct.sizeof(_lib.RRCGReport), dtype=torch.uint8, device="cuda")
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.gj_rrcg_report_device(sv._h, ct.c_void_p(buf.data_ptr()), stream) == 0
+    host = bytes(buf.cpu().numpy().tobytes())
+    dev = _lib.RRCGReport.from_buffer_copy(host)
+    rep = sv.report()
+    assert dev.iterations == rep["iterations"] == 4 and dev.status == rep["status"] == 0
+    assert list(dev.phi) == rep["phi"] and dev.S_G == rep["S_G"] and list(dev.alpha) == rep["alpha"]
+    sv.close()

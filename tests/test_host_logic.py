@@ -1,6 +1,5 @@
 """Host-side logic of the binding, on the CPU: the autotuner's padded-size
-candidates, the Pearson coefficient of the lambda sweep, and the solver-option
-mapping.  None of these calls the GPU."""
+candidates and the solver-option mapping.  None of these calls the GPU."""
 import numpy as np
 import pytest
 
@@ -8,7 +7,6 @@ import synth
 from paper_2112_15562_gb300 import _lib as L
 from paper_2112_15562_gb300 import autotune
 from paper_2112_15562_gb300.api import solver_params
-from paper_2112_15562_gb300.sweep import pearson
 
 
 def _smooth(n, primes=(2, 3, 5, 7)):
@@ -37,16 +35,6 @@ def test_candidates_cover_the_bccb_size_and_the_512_kernels():
     assert (512, 512) in autotune.candidates(g2, "fp32")
     g3 = synth.uniform_grid(300, 300, 300, 300, 4, 50.0)  # beyond the 512 kernels' 256 per side
     assert (512, 512) not in autotune.candidates(g3, "fp32")
-
-
-def test_pearson():
-    rng = np.random.default_rng(7)
-    a, b = rng.standard_normal(500), rng.standard_normal(500)
-    assert pearson(a, b) == pytest.approx(np.corrcoef(a, b)[0, 1], abs=1e-12)
-    assert pearson(a, 3.0 * a - 2.0) == pytest.approx(1.0, abs=1e-12)
-    assert pearson(a, -0.5 * a + 7.0) == pytest.approx(-1.0, abs=1e-12)
-    assert pearson(a, np.full(500, 4.0)) == 0.0  # no spread: defined as 0
-    assert pearson(2 * a + 1, 5 * b - 3) == pytest.approx(pearson(a, b), abs=1e-12)
 
 
 def test_solver_params_option_mapping():
