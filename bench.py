@@ -600,13 +600,23 @@ def c5_leg(gj, torch, dev, flush, hbm):
     layer's spectrum rebuilt from the closed forms inside each product."""
     import synth
 
+    import tempfile
+
+    from paper_2112_15562_gb300 import autotune
+
     g = synth.uniform_grid(512, 512, 512, 512, 48, 100.0)
     mag = synth.Mag(50000.0, 60.0, 10.0)
-    out = {"workload": "fwd+bwd of both fields at 512x512x48 (N=1024), FP32, L2 flushed per step"}
+    cache = os.path.join(tempfile.gettempdir(), "gj_autotune_bench.json")
+    npad, tiles = autotune.tune_full(g, mag, "fp32", cache=cache, reps=2)
+    out = {"workload": "fwd+bwd of both fields at 512x512x48, FP32, L2 flushed per step",
+           "npad_autotuned": list(npad), "tiles": tiles}
     for mode, steps in (("stored", 5), ("recomputed", 2)):
         t0 = time.perf_counter()
-        ops = [gj.bttb_setup(g, "gravity", precision="fp32", recompute=mode == "recomputed"),
-               gj.bttb_setup(g, "magnetic", mag, precision="fp32", recompute=mode == "recomputed")]
+        ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=npad, recompute=mode == "recomputed"),
+               gj.bttb_setup(g, "magnetic", mag, precision="fp32", npad=npad, recompute=mode == "recomputed")]
+        for o_ in ops:
+            if tiles:
+                o_.tune(**tiles)
         t_setup = time.perf_counter() - t0
         m = [torch.rand(g.n, device=dev, requires_grad=True) for _ in range(2)]
         gd = [torch.randn(g.s, device=dev) for _ in range(2)]
