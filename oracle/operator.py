@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .prism import FAR, prism_dT, prism_dT_cubature, prism_gz, prism_gz_cubature
+from .prism import FAR, cubature_order, prism_dT, prism_dT_cubature, prism_gz, prism_gz_cubature
 
 GRAVITY = 1
 MAGNETIC = 2
@@ -43,8 +43,8 @@ def _kernel(field, mag, x0, y0, z0, x1, x2, y1, y2, z1, z2):
         out[near] = prism_gz(*args(near))
     else:
         out[near] = prism_dT(*args(near), mag.F, mag.incl, mag.decl)
-    order = np.where(near, 0, np.where(dist < 2.0 * FAR * size, 5, 4))  # prism.cubature_order
-    for n in (5, 4):
+    order = np.where(near, 0, cubature_order(dist, size))
+    for n in (5, 4, 3):
         m = order == n
         if not m.any():
             continue

@@ -68,8 +68,9 @@ __global__ void k_corner_lattice(Lattice L, int magnetic, MagCoef mc, double *ou
 // Far from the station the 8-corner sums cancel (their terms grow like R log R
 // while the field falls like 1/R^2): a prism whose centre is at least kFar times its
 // largest side away is integrated by tensor Gauss-Legendre cubature of the smooth
-// integrand instead, 5 points per axis up to 2 kFar sides and 4 beyond (relative
-// error about 1e-13 there, against 1e-7 for the corner sums at 100 sides).
+// integrand instead, 5 points per axis up to 3 kFar sides, 4 up to 8 kFar and 3
+// beyond (relative error at most about 5e-13 there, against 1e-7 for the corner
+// sums at 100 sides).
 constexpr double kFar = 8.0;
 // Gauss-Legendre nodes and weights on [-1, 1]
 __constant__ double kGL5x[5] = {-0.90617984593866399280, -0.53846931010568309104, 0.0, 0.53846931010568309104,
@@ -80,6 +81,8 @@ __constant__ double kGL4x[4] = {-0.86113631159405257522, -0.33998104358485626480
                                 0.86113631159405257522};
 __constant__ double kGL4w[4] = {0.34785484513745385737, 0.65214515486254614263, 0.65214515486254614263,
                                 0.34785484513745385737};
+__constant__ double kGL3x[3] = {-0.77459666924148337704, 0.0, 0.77459666924148337704};
+__constant__ double kGL3w[3] = {0.55555555555555555556, 0.88888888888888888889, 0.55555555555555555556};
 
 // The integral over [u1, u2] x [v1, v2] x [w1, w2] of w / R^3 (gravity) or of
 // t^T (d2(1/R)/dr dr) t = (c0 (3u^2 - R^2) + c1 (3v^2 - R^2) + c2 (3w^2 - R^2)
@@ -87,8 +90,8 @@ __constant__ double kGL4w[4] = {0.34785484513745385737, 0.65214515486254614263, 
 template <int NP>
 __device__ double far_cubature(double uc, double hu, double vc, double hv, double wc, double hw, int magnetic,
                                const MagCoef &k) {
-    const double *x = NP == 5 ? kGL5x : kGL4x;
-    const double *wt = NP == 5 ? kGL5w : kGL4w;
+    const double *x = NP == 5 ? kGL5x : (NP == 4 ? kGL4x : kGL3x);
+    const double *wt = NP == 5 ? kGL5w : (NP == 4 ? kGL4w : kGL3w);
     double s = 0.0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
@@ -146,9 +149,11 @@ struct LoadTable {
             const double size = fmax(fmax(dx, dy), w2 - w1);
             const double dist = sqrt(uc * uc + vc * vc + wc * wc);
             if (dist >= kFar * size) {
-                const double v = dist < 2.0 * kFar * size
+                const double v = dist < 3.0 * kFar * size
                                      ? far_cubature<5>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
-                                     : far_cubature<4>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc);
+                                 : dist < 8.0 * kFar * size
+                                     ? far_cubature<4>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
+                                     : far_cubature<3>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc);
                 return v * scale;
             }
         }

@@ -145,7 +145,9 @@ def test_cubature_equals_closed_form_where_both_hold(off):
 @pytest.mark.parametrize("off", [(20.0, 7.0, 3.5), (60.0, 60.0, 30.5), (150.0, 90.0, 12.5)])
 def test_cubature_converges_far_out(off):
     x1, x2, y1, y2, z1, z2 = _box(off)
-    for n_lo, n_hi in ((4, 6), (5, 7)):
+    dist = np.linalg.norm([0.5 * (x1 + x2), 0.5 * (y1 + y2), 0.5 * (z1 + z2)])
+    n_rule = int(prism.cubature_order(dist, 100.0))
+    for n_lo, n_hi in ((n_rule, 7), (5, 7)):
         a = prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, n=n_lo)
         b = prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, n=n_hi)
         assert a == pytest.approx(b, rel=2e-13)
