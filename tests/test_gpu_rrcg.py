@@ -244,3 +244,33 @@ def test_host_buffer_solve_matches_oracle(small, prec):
     tol = 1e-9 if prec == "fp64" else 1e-3
     for i in range(2):
         assert rel(m[i], ref.m[i]) <= tol, (i, rel(m[i], ref.m[i]))
+
+
+@pytest.mark.parametrize("path", [("fp64", (0, 0)), ("fp32", (512, 512))])
+def test_solve_with_padding_prisms_and_non_square_grid(path):
+    """Stations a subset of the surface prisms (padding prisms left of and below the
+    first station, Sec. 2.7.1), dx != dy, variable layer thickness, one layer group
+    of 9 rows: the joint solve against the FP64 oracle on both kernel families."""
+    gj = lib()
+    prec, npad = path
+    g = synth.uniform_grid(11, 9, 14, 13, 5, 40.0, off_x=2, off_y=3)
+    g.dy = 55.0
+    g.z_edges = np.concatenate([[0.0], np.cumsum(np.linspace(25.0, 70.0, g.nz))])
+    mag = synth.Mag(50000.0, 60.0, 10.0)
+    A = [oop.dense_matrix(g, oop.GRAVITY), oop.dense_matrix(g, oop.MAGNETIC, mag)]
+    mt = [synth.smooth_blocky(g, 0.8, 71, n_boxes=2, sigma=2.0), synth.smooth_blocky(g, 0.08, 72, n_boxes=2, sigma=2.0)]
+    e = synth.standard_normal((2, g.s), 73)
+    obs = [owt.noisy_data(A[i] @ mt[i], 0.01, 0.01, e[i]) for i in range(2)]
+    dob, sig = [o[0] for o in obs], [o[1] for o in obs]
+    wdep = [owt.depth_weights(g.z_edges, 2.0), owt.depth_weights(g.z_edges, 3.0)]
+    kw = dict(KW, kmax=15)
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw))
+    w = synth.Workload("padded", g, mag, tuple(mt), (e[0], e[1]))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, prec, kw, npad=npad)
+    assert rep["iterations"] == 15
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    for k in range(16):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=tol), (k, i)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= (1e-9 if prec == "fp64" else 1e-3), (i, rel(m[i], ref.m[i]))
