@@ -194,3 +194,21 @@ def test_cubature_against_extended_precision_corner_sums():
         x1, x2, y1, y2, z1, z2 = _box(off)
         ref = gz_ld(x1, x2, y1, y2, z1, z2)
         assert prism.prism_gz_cubature(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2) == pytest.approx(ref, rel=1e-11)
+
+
+def test_cubature_with_an_offset_lifted_station():
+    """The cubature measures the prism from the station: moving both together changes
+    nothing, and with a station above the mesh (z0 < 0) it still equals the closed
+    form 8-12 sizes out."""
+    x1, x2, y1, y2, z1, z2 = _box((7.0, 5.0, 4.5))
+    x0, y0, z0 = 321.0, -47.0, -15.0
+    for fun, extra in ((prism.prism_gz_cubature, ()), (prism.prism_dT_cubature, (5e4, 60.0, 10.0))):
+        a = fun(0.0, 0.0, 0.0, x1, x2, y1, y2, z1, z2, *extra)
+        b = fun(x0, y0, z0, x1 + x0, x2 + x0, y1 + y0, y2 + y0, z1 + z0, z2 + z0, *extra)
+        assert b == pytest.approx(a, rel=1e-13)
+    g_c = prism.prism_gz(x0, y0, z0, x1, x2, y1, y2, z1, z2)
+    g_q = prism.prism_gz_cubature(x0, y0, z0, x1, x2, y1, y2, z1, z2)
+    assert g_q == pytest.approx(g_c, rel=1e-10)
+    m_c = prism.prism_dT(x0, y0, z0, x1, x2, y1, y2, z1, z2, 5e4, 60.0, 10.0)
+    m_q = prism.prism_dT_cubature(x0, y0, z0, x1, x2, y1, y2, z1, z2, 5e4, 60.0, 10.0)
+    assert m_q == pytest.approx(m_c, rel=1e-10)
