@@ -252,13 +252,17 @@ def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
     return world * steps / (max_total_ms / 1e3)
 
 
-def build_problem(gj, torch, prec, dev):
+def build_problem(gj, torch, prec, dev, npad=(0, 0), tiles=None):
     import numpy as np
     import synth
 
     w = synth.joint_256()
     g = w.grid
-    ops = [gj.bttb_setup(g, "gravity", precision=prec), gj.bttb_setup(g, "magnetic", w.mag, precision=prec)]
+    ops = [gj.bttb_setup(g, "gravity", precision=prec, npad=npad),
+           gj.bttb_setup(g, "magnetic", w.mag, precision=prec, npad=npad)]
+    for o_ in ops:
+        if tiles:
+            o_.tune(**tiles)
     dt = ops[0].dtype
     m_true = [torch.from_numpy(x).to(dt).to(dev) for x in w.m_true]
     d_ex = [ops[i].forward(m_true[i]) for i in range(2)]
@@ -472,9 +476,18 @@ def operator_leg(torch, ops, g, dev, flush, hbm, steps=50, elem=4):
 
 
 def fp64_leg(gj, torch, dev, flush, v32, hbm, alu, steps=8, warmup=2):
-    """The plain FP64 form (every vector, spectrum and FFT in FP64, generic kernels):
-    the RRCG iteration and the standalone G m + G^T r of both fields."""
-    w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp64", dev)
+    """The plain FP64 form (every vector, spectrum and FFT in FP64, general kernels with
+    the autotuned padded size, radix plan and tiles): the RRCG iteration and the
+    standalone G m + G^T r of both fields."""
+    import tempfile
+
+    import synth
+    from paper_2112_15562_gb300 import autotune
+
+    wt = synth.joint_256()
+    cache = os.path.join(tempfile.gettempdir(), "gj_autotune_bench.json")
+    npad, tiles = autotune.tune_full(wt.grid, wt.mag, "fp64", cache=cache, reps=2)
+    w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp64", dev, npad=npad, tiles=tiles)
     sv, m, P = solver_for(gj, torch, ops, g, dobs, sigma, wdep, steps + warmup + 2, dev)
     times, _, _ = time_steps(torch, sv, steps, warmup, flush, profile=False)
     sv.close()
@@ -483,10 +496,11 @@ def fp64_leg(gj, torch, dev, flush, v32, hbm, alu, steps=8, warmup=2):
     for o in ops:
         o.close()
     out = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "fp32_speedup": v32 / (1e3 / ms), "dtype": "f64 (plain FP64 form)", "operator": opl}
+           "fp32_speedup": v32 / (1e3 / ms), "dtype": "f64 (plain FP64 form)", "operator": opl,
+           "npad_autotuned": list(npad), "tiles": tiles}
     # FFT flops of one iteration (5 N log2 N per complex 512-point transform, the
     # transforms of the generic kernels: row and column passes of 6 products)
-    fl = iteration_fft_flops(g)
+    fl = iteration_fft_flops(g, N=max(npad))
     out["fft_GFLOPs_per_iteration"] = fl / 1e9
     if alu and alu.get("fp64_fma_tflops"):
         out["frac_of_fp64_fma_peak"] = fl / (ms * 1e-3) / 1e12 / alu["fp64_fma_tflops"]
