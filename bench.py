@@ -446,17 +446,18 @@ def operator_leg(torch, ops, g, dev, flush, hbm, steps=50, elem=4):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     res = {}
+    import paper_2112_15562_gb300 as gj
+
     for name in ("forward", "adjoint"):
         ts = []
         for k in range(steps + 3):
             if flush is not None:
                 flush.fill_(float(k))
             e0.record()
-            for i in range(2):
-                if name == "forward":
-                    ops[i].forward(m[i], d[i])
-                else:
-                    ops[i].adjoint(r[i], a[i])
+            if name == "forward":
+                gj.g_forward_pair(ops, m, d)
+            else:
+                gj.g_adjoint_pair(ops, r, a)
             e1.record()
             e1.synchronize()
             if k >= 3:
@@ -471,8 +472,8 @@ def operator_leg(torch, ops, g, dev, flush, hbm, steps=50, elem=4):
     gbs = 2 * per_pair / (tot * 1e-3) / 1e9
     return {"forward_pair_ms": res["forward"], "adjoint_pair_ms": res["adjoint"],
             "algorithmic_bytes_fwd_plus_adj": 2 * per_pair, "algorithmic_GBs": gbs, "frac_of_hbm": gbs / hbm,
-            "note": f"both fields, standalone C-ABI calls, {'L2 flushed' if flush is not None else 'warm'}, "
-                    f"medians of {steps}"}
+            "note": f"both fields per C-ABI call (gj_g_forward_pair / gj_g_adjoint_pair), "
+                    f"{'L2 flushed' if flush is not None else 'warm'}, medians of {steps}"}
 
 
 def fp64_leg(gj, torch, dev, flush, v32, hbm, alu, steps=8, warmup=2):

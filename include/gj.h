@@ -198,6 +198,22 @@ gj_status gj_g_forward(const gj_op *op, const void *m, void *d, gj_stream_t stre
 gj_status gj_g_adjoint(const gj_op *op, const void *r, void *g, gj_stream_t stream);
 
 /*
+ * gj_g_forward_pair / gj_g_adjoint_pair - the products of two operators in one
+ * call: d[i] = A_i m[i] (or g[i] = A_i^T r[i]) for i = 0, 1, with the vectors as in
+ * gj_g_forward / gj_g_adjoint.  When both operators are on the 512 x 512 fast path
+ * with the same grid (the gravity and magnetic operators of one joint problem), the
+ * persistent column passes take both fields' columns in one launch, which fills the
+ * GPU better than two single-field calls; the row passes stay per field, so that
+ * the results round as the single-field products do.  Otherwise the call runs the
+ * two products one after the other.  The two operators must differ
+ * (each owns its workspace); failures as for the single products.
+ */
+gj_status gj_g_forward_pair(const gj_op *const ops[2], const void *const m[2], void *const d[2],
+                            gj_stream_t stream);
+gj_status gj_g_adjoint_pair(const gj_op *const ops[2], const void *const r[2], void *const g[2],
+                            gj_stream_t stream);
+
+/*
  * gj_gramian_value_grad - the Gramian coupling (Eq. Gramian, RRCG:2-3).
  * S = (m1,m1)(m2,m2) - (m1,m2)^2 written to the device double *S, and the
  * ascent directions l1 = (m2,m2) m1 - (m1,m2) m2, l2 = (m1,m1) m2 - (m1,m2) m1

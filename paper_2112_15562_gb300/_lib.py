@@ -83,6 +83,8 @@ def load() -> ct.CDLL:
         "gj_selftest_bounded_wait": (i32, [i64, vp]),
         "gj_g_forward": (i32, [vp, vp, vp, vp]),
         "gj_g_adjoint": (i32, [vp, vp, vp, vp]),
+        "gj_g_forward_pair": (i32, [pp, pp, pp, vp]),
+        "gj_g_adjoint_pair": (i32, [pp, pp, pp, vp]),
         "gj_gramian_value_grad": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),
         "gj_gramian_value_grad_noalloc": (i32, [i64, i32, vp, vp, vp, vp, vp, vp]),
         "gj_rrcg_joint_solve": (i32, [pp, ct.POINTER(RRCGParams), pp, pp, pp, pp, pp, pp, vp,

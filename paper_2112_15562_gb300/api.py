@@ -116,6 +116,38 @@ def g_adjoint(op: Op, r: torch.Tensor, g: Optional[torch.Tensor] = None, stream=
     return g
 
 
+def g_forward_pair(ops: Sequence[Op], m, d=None, stream=None):
+    """gj_g_forward_pair: d[i] = A_i m[i] for both operators in one call."""
+    if ops[0] is ops[1]:
+        raise ValueError("the two operators must differ")
+    for i in range(2):
+        _vec(m[i], ops[i].dtype, ops[i].n, f"m[{i}]")
+    if d is None:
+        d = [torch.empty(ops[i].s, dtype=ops[i].dtype, device=m[i].device) for i in range(2)]
+    for i in range(2):
+        _vec(d[i], ops[i].dtype, ops[i].s, f"d[{i}]")
+    handles = (ct.c_void_p * 2)(ops[0].handle.value, ops[1].handle.value)
+    check(load().gj_g_forward_pair(handles, (ct.c_void_p * 2)(m[0].data_ptr(), m[1].data_ptr()),
+                                   (ct.c_void_p * 2)(d[0].data_ptr(), d[1].data_ptr()), _stream(stream)))
+    return d
+
+
+def g_adjoint_pair(ops: Sequence[Op], r, g=None, stream=None):
+    """gj_g_adjoint_pair: g[i] = A_i^T r[i] for both operators in one call."""
+    if ops[0] is ops[1]:
+        raise ValueError("the two operators must differ")
+    for i in range(2):
+        _vec(r[i], ops[i].dtype, ops[i].s, f"r[{i}]")
+    if g is None:
+        g = [torch.empty(ops[i].n, dtype=ops[i].dtype, device=r[i].device) for i in range(2)]
+    for i in range(2):
+        _vec(g[i], ops[i].dtype, ops[i].n, f"g[{i}]")
+    handles = (ct.c_void_p * 2)(ops[0].handle.value, ops[1].handle.value)
+    check(load().gj_g_adjoint_pair(handles, (ct.c_void_p * 2)(r[0].data_ptr(), r[1].data_ptr()),
+                                   (ct.c_void_p * 2)(g[0].data_ptr(), g[1].data_ptr()), _stream(stream)))
+    return g
+
+
 def gramian_value_grad(m1: torch.Tensor, m2: torch.Tensor, want_dirs: bool = True, stream=None):
     """gj_gramian_value_grad: returns (S as a 1-element float64 CUDA tensor, l1, l2)."""
     if m1.dtype not in (torch.float32, torch.float64) or m2.dtype != m1.dtype:

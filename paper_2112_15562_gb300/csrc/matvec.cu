@@ -106,6 +106,50 @@ static void fast_adjoint(const gj_op *o, const float *r, float *g, cudaStream_t 
     row_inv_t<float, true>(V, o->col_grid, o->nz, o->ny, o->nx, 0, StorePlain<float>{g, g, o->nx}, nullptr, st);
 }
 
+// Both fields of a joint problem with shared column passes: the row and data-line
+// passes run per field (two lines of one field per complex transform, as in the
+// single-field products), because a complex transform that carried a line of each
+// field would mix their rounding errors (the magnetic data are typically some 100
+// times the gravity data); the persistent column passes take both fields' columns in
+// one launch, where the fields never mix, which fills the GPU better than two
+// single-field column launches.
+static void fast_forward_pair(const gj_op *a, const gj_op *b, const float *m0, const float *m1, float *d0, float *d1,
+                              cudaStream_t st) {
+    using namespace f512;
+    View2<float> V = make_view2<float>(a, b);
+    View2<float> Va = make_view2<float>(a, nullptr), Vb = make_view2<float>(b, nullptr);
+    set_row_fwd_t_attr<float, LoadPlain<float>, true>();
+    set_row_inv_attr<float, StorePlain<float>, kDataNW, kDataFPW>();
+    set_col_attr<float>();
+    row_fwd_t<float, true>(Va, a->col_grid, a->nz, a->ny, a->nx, 0, LoadPlain<float>{m0, m0, a->nx}, nullptr, st);
+    row_fwd_t<float, true>(Vb, b->col_grid, b->nz, b->ny, b->nx, 0, LoadPlain<float>{m1, m1, b->nx}, nullptr, st);
+    col_fwd<float>(V, a->col_grid, nullptr, st);
+    row_inv<float, kDataNW, kDataFPW>(Va, 0, a->sy, a->sy, a->sx, 1, StorePlain<float>{d0, d0, a->sx}, nullptr, st);
+    row_inv<float, kDataNW, kDataFPW>(Vb, 0, b->sy, b->sy, b->sx, 1, StorePlain<float>{d1, d1, b->sx}, nullptr, st);
+}
+
+static void fast_adjoint_pair(const gj_op *a, const gj_op *b, const float *r0, const float *r1, float *g0, float *g1,
+                              cudaStream_t st) {
+    using namespace f512;
+    View2<float> V = make_view2<float>(a, b);
+    View2<float> Va = make_view2<float>(a, nullptr), Vb = make_view2<float>(b, nullptr);
+    set_row_fwd_attr<float, LoadPlain<float>, kDataNW, kDataFPW>();
+    set_row_inv_t_attr<float, StorePlain<float>, true>();
+    set_col_attr<float>();
+    row_fwd<float, kDataNW, kDataFPW>(Va, 0, a->sy, a->sy, a->sx, 2, LoadPlain<float>{r0, r0, a->sx}, nullptr, st);
+    row_fwd<float, kDataNW, kDataFPW>(Vb, 0, b->sy, b->sy, b->sx, 2, LoadPlain<float>{r1, r1, b->sx}, nullptr, st);
+    col_adj<float>(V, a->col_grid, nullptr, st);
+    row_inv_t<float, true>(Va, a->col_grid, a->nz, a->ny, a->nx, 0, StorePlain<float>{g0, g0, a->nx}, nullptr, st);
+    row_inv_t<float, true>(Vb, b->col_grid, b->nz, b->ny, b->nx, 0, StorePlain<float>{g1, g1, b->nx}, nullptr, st);
+}
+
+// Two operators serve one joint launch when both are on the fast path with the same
+// grid (their workspaces stay separate; the launch uses the first one's error word).
+static bool pair_eligible(const gj_op *a, const gj_op *b) {
+    return a != b && a->fast && b->fast && a->sx == b->sx && a->sy == b->sy && a->nx == b->nx && a->ny == b->ny &&
+           a->nz == b->nz && a->col_grid == b->col_grid;
+}
+
 gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {
     if (o->fast) fast_forward(o, (const float *)m, (float *)d, st);
     else if (o->prec == GJ_FP64) launch_forward<double>(o, (const double *)m, (double *)d, st);
@@ -183,4 +227,36 @@ extern "C" gj_status gj_selftest_bounded_wait(int64_t limit_ns, gj_stream_t stre
     cudaFree(err);
     if (e != cudaSuccess) return gj::cuda_fail(e, "gj_selftest_bounded_wait");
     return (gj_status)h;
+}
+
+extern "C" gj_status gj_g_forward_pair(const gj_op *const ops[2], const void *const m[2], void *const d[2],
+                                       gj_stream_t stream) {
+    if (!ops || !m || !d || !ops[0] || !ops[1] || !m[0] || !m[1] || !d[0] || !d[1]) {
+        gj::set_error("gj_g_forward_pair: NULL argument");
+        return GJ_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (gj::pair_eligible(ops[0], ops[1])) {
+        gj::fast_forward_pair(ops[0], ops[1], (const float *)m[0], (const float *)m[1], (float *)d[0], (float *)d[1], st);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GJ_OK : gj::cuda_fail(e, "gj_g_forward_pair launch");
+    }
+    gj_status rc = gj::forward_enqueue(ops[0], m[0], d[0], st);
+    return rc == GJ_OK ? gj::forward_enqueue(ops[1], m[1], d[1], st) : rc;
+}
+
+extern "C" gj_status gj_g_adjoint_pair(const gj_op *const ops[2], const void *const r[2], void *const g[2],
+                                       gj_stream_t stream) {
+    if (!ops || !r || !g || !ops[0] || !ops[1] || !r[0] || !r[1] || !g[0] || !g[1]) {
+        gj::set_error("gj_g_adjoint_pair: NULL argument");
+        return GJ_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (gj::pair_eligible(ops[0], ops[1])) {
+        gj::fast_adjoint_pair(ops[0], ops[1], (const float *)r[0], (const float *)r[1], (float *)g[0], (float *)g[1], st);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GJ_OK : gj::cuda_fail(e, "gj_g_adjoint_pair launch");
+    }
+    gj_status rc = gj::adjoint_enqueue(ops[0], r[0], g[0], st);
+    return rc == GJ_OK ? gj::adjoint_enqueue(ops[1], r[1], g[1], st) : rc;
 }
