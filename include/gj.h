@@ -82,7 +82,9 @@ typedef struct {
     int64_t spectrum_bytes;  /* device bytes of the stored layer spectra (one layer when
                                 recomputed per layer) */
     int64_t workspace_bytes; /* device bytes of the per-op workspace */
-    int fast_path;           /* 1: the specialised 512 x 512 kernels serve this op */
+    int fast_path;           /* 1: the specialised warp-FFT kernels serve this op (FP32,
+                                Nx = 512 and Ny = 512 or 256, at most Nx/2 prisms and
+                                stations along x and Ny/2 along y) */
     int P_row, C_col, L_grp; /* launch shapes of the general kernels (gj_op_tune) */
     int radix_order;         /* radix plan of the general kernels' transforms (gj_op_tune) */
     int recompute;           /* 1: spectra rebuilt per layer (GJ_SETUP_RECOMPUTE_SPECTRA) */
@@ -99,7 +101,10 @@ typedef struct {
  * operator's precision.  Npad_y/Npad_x = 0 selects the smallest size
  * >= s + n - 1 whose prime factors are all <= 7; otherwise each must be
  * >= s + n - 1 with prime factors <= 17 (any such size gives the same
- * product).  `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
+ * product).  In FP32, Npad = (512, 512) with at most 256 prisms and stations
+ * per direction, or (256, 512) with at most 128 along y, selects the specialised
+ * warp-FFT kernels (gj_op_info_t.fast_path); any other size runs the general ones.
+ * `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
  * Synchronous with respect to the host on return (the op is ready).
  * Returns GJ_ERR_ARG for invalid sizes, GJ_ERR_UNSUPPORTED for a padded size
  * above 2048 or with a larger prime factor, GJ_ERR_OOM if device memory runs
@@ -117,7 +122,7 @@ enum {
      * the operator's precision) just before using it (Sec. 2.7.1 applied per
      * layer).  The spectra are bit-identical to the stored ones; the cost is the
      * setup work of one layer per layer per product.  Served by the general
-     * kernels (never the 512 x 512 fast path); products only: the joint solver
+     * kernels (never the warp-FFT fast path); products only: the joint solver
      * rejects such operators with GJ_ERR_UNSUPPORTED. */
     GJ_SETUP_RECOMPUTE_SPECTRA = 1
 };
@@ -179,7 +184,7 @@ gj_status gj_selftest_bounded_wait(int64_t limit_ns, gj_stream_t stream);
  * (Sec. 2.7.1).  m: n values, d: s values, both of the op's precision;
  * m and d must not overlap.
  *
- * Device-side failures (this and gj_g_adjoint): on the 512 x 512 fast path the
+ * Device-side failures (this and gj_g_adjoint): on the warp-FFT fast path the
  * column kernels wait on their bulk copies with a bound (200 ms per wait).  A
  * wait that gives up records GJ_ERR_TIMEOUT in the operator's error word and
  * leaves d (or g) incomplete; every later fast-path column launch of that
@@ -200,8 +205,8 @@ gj_status gj_g_adjoint(const gj_op *op, const void *r, void *g, gj_stream_t stre
 /*
  * gj_g_forward_pair / gj_g_adjoint_pair - the products of two operators in one
  * call: d[i] = A_i m[i] (or g[i] = A_i^T r[i]) for i = 0, 1, with the vectors as in
- * gj_g_forward / gj_g_adjoint.  When both operators are on the 512 x 512 fast path
- * with the same grid (the gravity and magnetic operators of one joint problem), the
+ * gj_g_forward / gj_g_adjoint.  When both operators are on the warp-FFT fast path
+ * with the same grid and padded size (the gravity and magnetic operators of one joint problem), the
  * persistent column passes take both fields' columns in one launch, which fills the
  * GPU better than two single-field calls; the row passes stay per field, so that
  * the results round as the single-field products do.  Otherwise the call runs the

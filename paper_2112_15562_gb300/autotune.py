@@ -2,7 +2,8 @@
 
 Any padded size N >= s + n - 1 gives the same product (Sec. 2.7.1), so the choice
 is purely a speed question: a 512 x 512 embedding (for up to 256 prisms and
-stations per direction, FP32) selects the specialised warp-FFT kernels; other
+stations per direction, FP32), or 256 x 512 (at most 128 of them along y), selects
+the specialised warp-FFT kernels; other
 sizes run the general kernels, whose radix plan and tiles (line pairs per CTA of
 the row passes, columns per CTA of the column passes, layers per CTA of the
 spectrum multiply; gj_op_tune) are searched too.  ``tune_full`` times one forward
@@ -41,8 +42,13 @@ def candidates(grid, precision: str) -> List[Tuple[int, int]]:
     ys = smooth_sizes(grid.sy + grid.ny - 1)
     xs = smooth_sizes(grid.sx + grid.nx - 1)
     cands = list(zip(ys, xs))
-    if precision == "fp32" and max(grid.sx, grid.sy, grid.nx, grid.ny) <= 256 and (512, 512) not in cands:
-        cands.append((512, 512))
+    if precision == "fp32" and max(grid.sx, grid.nx) <= 256:
+        # the specialised kernels: N_x = 512, and N_y = 512 or, for at most 128
+        # stations and prisms per column, 256
+        if max(grid.sy, grid.ny) <= 256 and (512, 512) not in cands:
+            cands.append((512, 512))
+        if max(grid.sy, grid.ny) <= 128 and (256, 512) not in cands:
+            cands.append((256, 512))
     return cands
 
 

@@ -327,6 +327,7 @@ struct View2 {  // the two fields of a launch (field 1 unused in single-field la
     int nfield;
     int *err;
     const cpx<R> *twtab;  // the column kernels' twiddle table (TabTw layout), built once per operator
+    int hy;               // column stride of Zt, Wt and Vt: Ny / 2 (256 or 128)
 };
 
 // Every CTA of a column kernel copies the operator's twiddle table into shared
@@ -609,12 +610,323 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     if (!ok) drain(bars[warp], t_fail, t0, t1, V.err);
 }
 
+// ---------------------------------------------------------------------------
+// Column passes of the 256-row embedding (N_y = 256, at most 128 prisms and 128
+// stations per column; the rows keep N_x = 512).  Each half-warp runs a pruned
+// 256-point transform of its own (inputs n < 128, the rest zero) on the 16 x 16
+// steps of the 512 transform without the parity split: lane (h, l) holds
+// x_h[l + 16 j], and after the second 16-point DFT lane (h, k2) holds
+// X_h[k2 + 16 k1] in register k1.  The two half-warps take two layers of the same
+// column, so an item is a layer pair (2 rp, 2 rp + 1) and the register, stage and
+// transpose footprint equals the 512 kernels'.  Layouts: Zt[r][kx][iy < 128],
+// St[r][kx][ky < 256], Wt/Vt[kx][jy < 128].
+
+constexpr int N2 = 256, H2 = 128;
+
+// Forward pruned 256-point transform of this half-warp's column.  In: v[j] =
+// x[l + 16 j] for j < 8 (v[8..15] ignored, taken as zero).  Out: v[k1] = X[k2 + 16 k1].
+template <typename R, class TW>
+__device__ __forceinline__ void fwd256h(cpx<R> (&v)[16], cpx<R> *buf, const TW &tw) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    cpx<R> *t = buf + h * 256;
+#pragma unroll
+    for (int j = 8; j < 16; ++j) v[j] = czero<cpx<R>>();
+    dft16<R, false>(v);  // over j -> index a; the zero half folds away
+#pragma unroll
+    for (int k = 1; k < 16; ++k) v[k] = tw.template mul256<false>(v[k], k);  // W256^(l a)
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t[swz(l, k)] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = t[swz(r, l)];
+    dft16<R, false>(v);  // over l -> index b: X[a + 16 b], a = this lane's l
+}
+
+// Inverse 256-point transform of this half-warp's column (unnormalised).
+// In: v[k1] = Y[k2 + 16 k1].  Out: v[j] = y[l + 16 j], j < 16.
+template <typename R, class TW>
+__device__ __forceinline__ void inv256h(cpx<R> (&v)[16], cpx<R> *buf, const TW &tw) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, k2 = lane & 15;
+    cpx<R> *t = buf + h * 256;
+    dft16<R, true>(v);  // over k1 -> index l
+#pragma unroll
+    for (int l = 1; l < 16; ++l) v[l] = tw.template mul256<true>(v[l], l);  // W256^-(l k2)
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) t[swz(k2, l)] = v[l];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = t[swz(r, k2)];
+    dft16<R, true>(v);  // over k2 -> index j
+}
+
+// Forward column pass, N_y = 256: for each (field, kx), Y = sum_r St_r[kx] . FFT256(Zt_r[kx]),
+// then W[kx][jy] = IFFT256(Y)[jy] for jy < sy.  Items are (kx, field, layer pair) in
+// the order of k_col_fwd512; the two half-warps' sums meet at the end of a column.
+template <typename R>
+__global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd256(View2<R> V, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done) || op_failed(V.err)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int ZB = H2 * sizeof(C), TB = N2 * sizeof(C);  // one layer's column of Zt / St
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    unsigned char *wbase = smem_raw + (size_t)warp * (CSTAGES * 2 * (ZB + TB) + N * sizeof(C));
+    C *zs = reinterpret_cast<C *>(wbase);                              // CSTAGES x 2 x 128
+    C *ts = reinterpret_cast<C *>(wbase + CSTAGES * 2 * ZB);           // CSTAGES x 2 x 256
+    C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * 2 * (ZB + TB));  // 512
+    C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * 2 * (ZB + TB) + N * sizeof(C)));
+    __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
+    __shared__ __align__(8) uint64_t tabbar;
+    if (lane == 0)
+        for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
+    if (threadIdx.x == 0) mbar_init(&tabbar);
+    mbar_fence_init();
+    __syncthreads();
+    TabTw<R> tw;
+    tw.bind(tab);
+    const int nz = V.op[0].nz, sy = V.op[0].sy, nzp = (nz + 1) >> 1;
+    const long long T = (long long)V.nfield * NC * nzp;
+    const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
+    const long long w = (long long)blockIdx.x * CWARPS + warp;
+    if ((long long)blockIdx.x * CWARPS < Wt) load_twtab<R>(tab, V.twtab, &tabbar);
+    if (w >= Wt) return;
+    const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
+    ColItem cu, ci;  // r counts layer pairs
+    cu.set(t0, nzp, V.nfield);
+    ci = cu;
+    int ti = t0;
+    auto issue = [&]() {  // the layer pair of item ti into stage (ti - t0) % CSTAGES
+        const int s = (ti - t0) % CSTAGES;
+        const OpView<R> &op = V.op[ci.fld];
+        const int r0 = 2 * ci.r, nl = r0 + 1 < nz ? 2 : 1;
+        const size_t off = (size_t)r0 * NC + ci.kx;
+        const uint32_t tb = op.real_spec ? TB / 2 : TB;
+        mbar_expect(&bars[warp][s], nl * (ZB + tb));
+        for (int i = 0; i < nl; ++i) {
+            const size_t o = off + (size_t)i * NC;
+            bulk_load(zs + (s * 2 + i) * H2, op.Z + o * H2, ZB, &bars[warp][s]);
+            if (op.real_spec)
+                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * N2, reinterpret_cast<const R *>(op.spec) + o * N2,
+                          tb, &bars[warp][s]);
+            else
+                bulk_load(ts + (s * 2 + i) * N2, op.spec + o * N2, tb, &bars[warp][s]);
+        }
+        ++ti;
+        ci.next(nzp, V.nfield);
+    };
+    if (lane == 0)
+        while (ti < t1 && ti < t0 + CSTAGES) issue();
+    C acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = czero<C>();
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&tabbar, 0, V.err));
+    int t_fail = ok ? t1 : t0;
+    int seg_start = t0;
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nzp, V.nfield)) {
+        const int s = (t - t0) % CSTAGES;
+        const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
+        if (!ok) { t_fail = t; break; }
+        const bool mine = 2 * cu.r + h < nz;  // this half-warp's layer exists
+        C v[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = zs[(s * 2 + h) * H2 + l + 16 * j];
+        fwd256h<R>(v, xbuf, tw);
+        if (mine) {
+            if (V.op[cu.fld].real_spec) {
+                const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * N2;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const R tt = tr[l + 16 * k1];
+                    acc[k1] = mk<C>(acc[k1].x + v[k1].x * tt, acc[k1].y + v[k1].y * tt);
+                }
+            } else {
+                const C *tc = ts + (s * 2 + h) * N2;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const C tt = tc[l + 16 * k1];
+                    acc[k1].x = fma(v[k1].x, tt.x, acc[k1].x);
+                    acc[k1].x = fma(-v[k1].y, tt.y, acc[k1].x);
+                    acc[k1].y = fma(v[k1].x, tt.y, acc[k1].y);
+                    acc[k1].y = fma(v[k1].y, tt.x, acc[k1].y);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && ti < t1) issue();
+        if (cu.r == nzp - 1 || t == t1 - 1) {
+            // end of this warp's part of column `col`: the half-warps' layer sums meet
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                acc[k1].x += __shfl_xor_sync(0xffffffffu, acc[k1].x, 16);
+                acc[k1].y += __shfl_xor_sync(0xffffffffu, acc[k1].y, 16);
+            }
+            const int fld = cu.fld, kx = cu.kx;
+            const long long col = cu.col;
+            const OpView<R> &op = V.op[fld];
+            const long long cb = col * nzp, ce = cb + nzp - 1;
+            const bool whole = (seg_start <= cb) && (t == ce);
+            if (!whole) {
+                const long long wf = seg_owner(cb, T, Wt), wl = seg_owner(ce, T, Wt);
+                const int slot = (int)(w - wf), nslots = (int)(wl - wf + 1);
+                C *Pc = V.P[fld] + (size_t)kx * V.slots * N2;
+#pragma unroll
+                for (int k1 = 0; k1 < 8; ++k1)  // registers chosen by selects, not by a runtime index
+                    Pc[(size_t)slot * N2 + l + 16 * (8 * h + k1)] = h ? acc[8 + k1] : acc[k1];
+                __threadfence();
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(V.cnt[fld] + kx, 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == nslots - 1) {
+                    __threadfence();
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+                    for (int sl = 0; sl < nslots; ++sl) {
+#pragma unroll
+                        for (int k1 = 0; k1 < 16; ++k1)
+                            acc[k1] = cadd(acc[k1], __ldcg(Pc + (size_t)sl * N2 + l + 16 * k1));
+                    }
+                    if (lane == 0) V.cnt[fld][kx] = 0;
+                } else {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+                    seg_start = t + 1;
+                    continue;
+                }
+            }
+            // both half-warps hold the column's sum; each writes half of the rows
+            inv256h<R>(acc, xbuf, tw);
+            C *Wc = op.W + (size_t)kx * H2;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int n = l + 16 * (4 * h + jj);
+                if (n < sy) Wc[n] = h ? acc[4 + jj] : acc[jj];
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) acc[k1] = czero<C>();
+            seg_start = t + 1;
+        }
+    }
+    if (!ok) drain(bars[warp], t_fail, t0, t1, V.err);
+}
+
+// Adjoint column pass, N_y = 256: for each (field, kx, r),
+// Zt_r[kx][iy] = IFFT256(conj(St_r[kx]) . FFT256(Vt[kx]))[iy], iy < ny; half-warp h
+// takes layer 2 rp + h of item (kx, field, rp).
+template <typename R>
+__global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj256(View2<R> V, const int *done) {
+    using C = cpx<R>;
+    if (stopped(done) || op_failed(V.err)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TB = N2 * sizeof(C);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    unsigned char *wbase = smem_raw + (size_t)warp * (CSTAGES * 2 * TB + N * sizeof(C));
+    C *ts = reinterpret_cast<C *>(wbase);                      // CSTAGES x 2 x 256
+    C *xbuf = reinterpret_cast<C *>(wbase + CSTAGES * 2 * TB);  // 512
+    C *tab = reinterpret_cast<C *>(smem_raw + (size_t)CWARPS * (CSTAGES * 2 * TB + N * sizeof(C)));
+    __shared__ __align__(8) uint64_t bars[CWARPS][CSTAGES];
+    __shared__ __align__(8) uint64_t tabbar;
+    if (lane == 0)
+        for (int s = 0; s < CSTAGES; ++s) mbar_init(&bars[warp][s]);
+    if (threadIdx.x == 0) mbar_init(&tabbar);
+    mbar_fence_init();
+    __syncthreads();
+    TabTw<R> tw;
+    tw.bind(tab);
+    const int nz = V.op[0].nz, ny = V.op[0].ny, nzp = (nz + 1) >> 1;
+    const long long T = (long long)V.nfield * NC * nzp;
+    const long long Wt = seg_warps((long long)gridDim.x * CWARPS, T);
+    const long long w = (long long)blockIdx.x * CWARPS + warp;
+    if ((long long)blockIdx.x * CWARPS < Wt) load_twtab<R>(tab, V.twtab, &tabbar);
+    if (w >= Wt) return;
+    const int t0 = (int)seg_begin(w, T, Wt), t1 = (int)seg_begin(w + 1, T, Wt);
+    ColItem cu, ci;  // r counts layer pairs
+    cu.set(t0, nzp, V.nfield);
+    ci = cu;
+    int ti = t0;
+    auto issue = [&]() {
+        const int s = (ti - t0) % CSTAGES;
+        const OpView<R> &op = V.op[ci.fld];
+        const int r0 = 2 * ci.r, nl = r0 + 1 < nz ? 2 : 1;
+        const size_t off = (size_t)r0 * NC + ci.kx;
+        const uint32_t tb = op.real_spec ? TB / 2 : TB;
+        mbar_expect(&bars[warp][s], nl * tb);
+        for (int i = 0; i < nl; ++i) {
+            const size_t o = off + (size_t)i * NC;
+            if (op.real_spec)
+                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * N2, reinterpret_cast<const R *>(op.spec) + o * N2,
+                          tb, &bars[warp][s]);
+            else
+                bulk_load(ts + (s * 2 + i) * N2, op.spec + o * N2, tb, &bars[warp][s]);
+        }
+        ++ti;
+        ci.next(nzp, V.nfield);
+    };
+    if (lane == 0)
+        while (ti < t1 && ti < t0 + CSTAGES) issue();
+    C vh[16];
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&tabbar, 0, V.err));
+    int t_fail = ok ? t1 : t0;
+    for (int t = t0; t < t1 && ok; ++t, cu.next(nzp, V.nfield)) {
+        const int fld = cu.fld, kx = cu.kx, r = 2 * cu.r + h;
+        const OpView<R> &op = V.op[fld];
+        if (t == t0 || cu.r == 0) {  // a new column: both half-warps transform it
+            const C *Vc = op.V + (size_t)kx * H2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vh[j] = Vc[l + 16 * j];
+            fwd256h<R>(vh, xbuf, tw);
+        }
+        const int s = (t - t0) % CSTAGES;
+        const uint32_t par = (uint32_t)(((t - t0) / CSTAGES) & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(&bars[warp][s], par, V.err));
+        if (!ok) { t_fail = t; break; }
+        const bool mine = r < nz;
+        C v[16];
+        if (!mine) {  // the stage holds no spectrum for this half-warp
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) v[k1] = czero<C>();
+        } else if (op.real_spec) {
+            const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * N2;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const R tt = tr[l + 16 * k1];
+                v[k1] = mk<C>(vh[k1].x * tt, vh[k1].y * tt);
+            }
+        } else {
+            const C *tc = ts + (s * 2 + h) * N2;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulc(vh[k1], tc[l + 16 * k1]);
+        }
+        __syncwarp();
+        if (lane == 0 && ti < t1) issue();
+        inv256h<R>(v, xbuf, tw);
+        if (mine) {
+            C *Zc = op.Z + ((size_t)r * NC + kx) * H2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n = l + 16 * j;
+                if (n < ny) Zc[n] = v[j];
+            }
+        }
+    }
+    if (!ok) drain(bars[warp], t_fail, t0, t1, V.err);
+}
+
 // shared-memory bytes of each kernel
 template <typename R> inline size_t smem_col_fwd() {
     return ((size_t)CWARPS * (CSTAGES * (H + N) + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
 }
 template <typename R> inline size_t smem_col_adj() {
     return ((size_t)CWARPS * (CSTAGES * N + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
+}
+// the 256-row kernels stage two layers of half the length: the same bytes
+template <typename R> inline size_t smem_col_fwd256() {
+    return ((size_t)CWARPS * (CSTAGES * 2 * (H2 + N2) + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
+}
+template <typename R> inline size_t smem_col_adj256() {
+    return ((size_t)CWARPS * (CSTAGES * 2 * N2 + N) + TabTw<R>::WORDS) * sizeof(cpx<R>);
 }
 
 }  // namespace f512

@@ -50,15 +50,16 @@ __device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const Vie
     pair_lines(joint, base, f, nlines, la, lb, ha, hb);
     const int fb = joint ? 1 : 0;
     const int ra = ha ? la / lpl : 0, rb = hb ? lb / lpl : 0;
-    C *oa = (out_sel == 0 ? V.op[0].Z : (out_sel == 1 ? V.op[0].W : V.op[0].V)) + (size_t)ra * NC * H + (la - ra * lpl);
-    C *ob = (out_sel == 0 ? V.op[fb].Z : (out_sel == 1 ? V.op[fb].W : V.op[fb].V)) + (size_t)rb * NC * H + (lb - rb * lpl);
+    const int hy = V.hy;
+    C *oa = (out_sel == 0 ? V.op[0].Z : (out_sel == 1 ? V.op[0].W : V.op[0].V)) + (size_t)ra * NC * hy + (la - ra * lpl);
+    C *ob = (out_sel == 0 ? V.op[fb].Z : (out_sel == 1 ? V.op[fb].W : V.op[fb].V)) + (size_t)rb * NC * hy + (lb - rb * lpl);
     const C *row = tile + f * (N + 1);
     const int kstep = blockDim.x / FFTS;
     for (int kx = threadIdx.x / FFTS; kx < NC; kx += kstep) {
         const C zk = row[ppos(kx)];
         const C zm = row[ppos((N - kx) & (N - 1))];
-        if (ha) oa[kx * H] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-        if (hb) ob[kx * H] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        if (ha) oa[kx * hy] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (hb) ob[kx * hy] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     }
 }
 
@@ -138,13 +139,14 @@ __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> 
     const bool ok = line < nlines;
     const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
     const C *src = in_sel == 0 ? V.op[fld].Z : (in_sel == 1 ? V.op[fld].W : V.op[fld].V);
-    const C *in = src + (size_t)r * NC * H + iy;
+    const int hy = V.hy;
+    const C *in = src + (size_t)r * NC * hy + iy;
     const int kx0 = threadIdx.x / SRC, kstep = blockDim.x / SRC;
     // every copy in flight at once; sources past the last line read as zero (their
     // lane may pair with a valid line in the same complex transform)
     for (int kx = kx0; kx < NC; kx += kstep) {
         C *dst = tile + kpos(kx) * P + s;
-        if (ok) cp_async8(dst, in + (size_t)kx * H);
+        if (ok) cp_async8(dst, in + (size_t)kx * hy);
         else *dst = czero<C>();
     }
     cp_async_commit();
@@ -284,35 +286,36 @@ __device__ __forceinline__ void split_to_stage(const cpx<R> (&v)[16], cpx<R> *sa
     }
 }
 
-// Slots g < ng of a team tile -> out[kx * H + g] (joint: field 0 to oa, field 1 to
-// ob; pair: eight slots to oa).  The team's 128 threads take (g, kx) =
+// Slots g < ng of a team tile -> out[kx * hy + g] (joint: field 0 to oa, field 1 to
+// ob; pair: eight slots to oa; hy = the column stride).  The team's 128 threads take (g, kx) =
 // (tid % GPT, tid / GPT + (128 / GPT) i): kx advances by 32 or 16, keeping its parity,
 // so kq(kx) advances by half of that.
 template <typename R, bool PAIR>
-__device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid) {
+__device__ __forceinline__ void team_store(const cpx<R> *stage, cpx<R> *oa, cpx<R> *ob, int ng, int tid, int hy) {
     constexpr int GPT = TeamMode<PAIR>::GPT, KS = 128 / GPT;
     const int g = tid % GPT;
     if (g >= ng) return;
     int kx = tid / GPT;
     const cpx<R> *sa = stage + g * (PAIR ? LSP : LS) + kq(kx);
-    size_t o = (size_t)kx * H + g;
-    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * H) {
+    size_t o = (size_t)kx * hy + g;
+    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * hy) {
         oa[o] = sa[0];
         if (!PAIR) ob[o] = sa[FS];
     }
 }
 
-// in[kx * H + g] -> slots g < ng of a team tile (asynchronous copies; layout as in
+// in[kx * hy + g] -> slots g < ng of a team tile (asynchronous copies; layout as in
 // team_store).
 template <typename R, bool PAIR>
-__device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid) {
+__device__ __forceinline__ void team_load(cpx<R> *stage, const cpx<R> *ia, const cpx<R> *ib, int ng, int tid,
+                                          int hy) {
     constexpr int GPT = TeamMode<PAIR>::GPT, KS = 128 / GPT;
     const int g = tid % GPT;
     if (g >= ng) return;
     int kx = tid / GPT;
     cpx<R> *sa = stage + g * (PAIR ? LSP : LS) + kq(kx);
-    size_t o = (size_t)kx * H + g;
-    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * H) {
+    size_t o = (size_t)kx * hy + g;
+    for (; kx < NC; kx += KS, sa += KS / 2, o += (size_t)KS * hy) {
         cp_async8(sa, ia + o);
         if (!PAIR) cp_async8(sa + FS, ib + o);
     }
@@ -470,8 +473,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, 
                 else split_to_stage<R>(v, tile + k * LS, tile + FS + k * LS);
             }
             team_barrier(team);  // the group's tile is complete; the other tile is free again
-            const size_t off = (size_t)r * NC * H + iy0;
-            team_store<R, PAIR>(tile, out0 + off, out1 + off, ng, tid);
+            const size_t off = (size_t)r * NC * V.hy + iy0;
+            team_store<R, PAIR>(tile, out0 + off, out1 + off, ng, tid, V.hy);
         }
     }
     pro.flush(red);
@@ -508,8 +511,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, 
         bool hb;
         group_lines(q0, gpl, lpl, LPG, r, iy0, ng);
         {
-            const size_t off = (size_t)r * NC * H + iy0;
-            team_load<R, PAIR>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid);
+            const size_t off = (size_t)r * NC * V.hy + iy0;
+            team_load<R, PAIR>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid, V.hy);
             cp_async_commit();
             if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) prefetch_rows(epi, pre, la, hb ? lb : -1, n_out);
             cp_async_commit();
@@ -521,8 +524,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, 
             if (q + 1 < q1) {
                 int r2, iy2, ng2;
                 group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
-                const size_t off = (size_t)r2 * NC * H + iy2;
-                team_load<R, PAIR>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid);
+                const size_t off = (size_t)r2 * NC * V.hy + iy2;
+                team_load<R, PAIR>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid, V.hy);
             }
             cp_async_commit();
             if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) {

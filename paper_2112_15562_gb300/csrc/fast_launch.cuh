@@ -1,4 +1,4 @@
-// Host-side launch helpers of the 512 x 512 fast path.
+// Host-side launch helpers of the fast path (N_x = 512; N_y = 512 or 256).
 #pragma once
 #include "fast512_rows.cuh"
 #include "view.cuh"
@@ -19,6 +19,7 @@ inline View2<R> make_view2(const gj_op *a, const gj_op *b) {
     V.nfield = b ? 2 : 1;
     V.err = a->err;
     V.twtab = static_cast<const cpx<R> *>(a->twtab);
+    V.hy = a->Ny / 2;
     return V;
 }
 
@@ -51,6 +52,8 @@ template <typename R>
 inline void set_col_attr() {
     allow_max_smem(k_col_fwd512<R>);
     allow_max_smem(k_col_adj512<R>);
+    allow_max_smem(k_col_fwd256<R>);
+    allow_max_smem(k_col_adj256<R>);
 }
 
 // out_sel / in_sel: 0 = Z, 1 = W, 2 = V
@@ -91,14 +94,21 @@ inline void row_inv_t(const View2<R> &V, int grid, int nz, int lpl, int n_out, i
         V, nz, lpl, n_out, in_sel, epi, done);
 }
 
+// the column passes of the operator's N_y (512 or 256)
 template <typename R>
 inline void col_fwd(const View2<R> &V, int grid, const int *done, cudaStream_t st) {
-    k_col_fwd512<R><<<grid, CWARPS * 32, smem_col_fwd<R>(), st>>>(V, done);
+    if (V.op[0].Ny == N2)
+        k_col_fwd256<R><<<grid, CWARPS * 32, smem_col_fwd256<R>(), st>>>(V, done);
+    else
+        k_col_fwd512<R><<<grid, CWARPS * 32, smem_col_fwd<R>(), st>>>(V, done);
 }
 
 template <typename R>
 inline void col_adj(const View2<R> &V, int grid, const int *done, cudaStream_t st) {
-    k_col_adj512<R><<<grid, CWARPS * 32, smem_col_adj<R>(), st>>>(V, done);
+    if (V.op[0].Ny == N2)
+        k_col_adj256<R><<<grid, CWARPS * 32, smem_col_adj256<R>(), st>>>(V, done);
+    else
+        k_col_adj512<R><<<grid, CWARPS * 32, smem_col_adj<R>(), st>>>(V, done);
 }
 
 }  // namespace f512

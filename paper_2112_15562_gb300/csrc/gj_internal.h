@@ -29,11 +29,11 @@ struct gj_op {
     // launch shapes
     int P_row = 8, C_col = 8, L_grp = 4;
     int radix_order = 0;
-    // 512 x 512 fast path (FP32, <= 256 prisms and stations per direction):
-    // transposed spectra and intermediates, layer-sum partials and counters
+    // fast path (FP32, N_x = 512 and N_y = 512 or 256, at most N/2 prisms and stations
+    // per direction): transposed spectra and intermediates, layer-sum partials and counters
     bool fast = false;
     bool real_spec = false;  // fast path: the table is even in both offsets, its spectrum is real
-    void *P = nullptr;     // [ncol][slots][512] complex
+    void *P = nullptr;     // [ncol][slots][Ny] complex
     int *cnt = nullptr;    // [ncol] arrival counters
     int *err = nullptr;    // device error word (bounded waits)
     void *twtab = nullptr; // the column kernels' twiddle table (FP32, TabTw layout)
@@ -63,7 +63,8 @@ template <typename R> OpView<R> view_of(const gj_op *op);
 
 // fast-path helpers (setup.cu)
 bool fast_eligible(const gj_op *op);
-int fast_slots(int nfield, int nz, int grid_ctas);
+int fast_col_items(int Ny, int nz);  // items per column of the fast column kernels
+int fast_slots(int nfield, int items_per_col, int grid_ctas);
 
 // rebuilds layer r's spectrum into spec (recompute mode; setup.cu)
 void recompute_layer(const gj_op *op, int r, cudaStream_t st);

@@ -147,7 +147,7 @@ static void fast_adjoint_pair(const gj_op *a, const gj_op *b, const float *r0, c
 // grid (their workspaces stay separate; the launch uses the first one's error word).
 static bool pair_eligible(const gj_op *a, const gj_op *b) {
     return a != b && a->fast && b->fast && a->sx == b->sx && a->sy == b->sy && a->nx == b->nx && a->ny == b->ny &&
-           a->nz == b->nz && a->col_grid == b->col_grid;
+           a->nz == b->nz && a->Ny == b->Ny && a->col_grid == b->col_grid;
 }
 
 gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {

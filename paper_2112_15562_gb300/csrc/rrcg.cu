@@ -1224,26 +1224,30 @@ extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj
     gj_rrcg_batch *b = new (std::nothrow) gj_rrcg_batch();
     if (!b) { set_error("gj_rrcg_batch_create: host allocation failed"); return GJ_ERR_OOM; }
     b->sv.assign(solvers, solvers + count);
-    // The branches run concurrently: the fast-path solvers share the SMs in proportion
-    // to their work (column items plus row lines per layer), so that their persistent
-    // kernels (one CTA per SM each) can be resident at the same time.  A smaller grid
-    // never needs more layer-sum slots than the operator holds (each warp's segment
-    // only grows); the check below keeps the full grid otherwise.
+    // The branches run concurrently: the fast-path solvers get grids in proportion to
+    // their work (column items, scaled by N_y, plus row lines per layer), so that their
+    // persistent kernels (one CTA per SM each) can be resident at the same time.  Each
+    // gets twice its proportional share: the branches finish at different times, and
+    // grids that add up to one CTA per SM leave SMs idle once the smaller problems are
+    // done.  A smaller grid never needs more layer-sum slots than the operator holds
+    // (each warp's segment only grows); the check below keeps the full grid otherwise.
     {
+        auto work = [](const gj_op *o) { return (double)o->nz * (2.0 * 257 * o->Ny / 512 + o->ny); };
         double tot = 0.0;
         int sms = 0;
         for (gj_rrcg *sv : b->sv)
             if (sv->op[0]->fast && sv->prec == GJ_FP32_MIXED) {
-                tot += (double)sv->op[0]->nz * (2.0 * 257 + sv->op[0]->ny);
+                tot += work(sv->op[0]);
                 sms = sv->op[0]->col_grid;
             }
         for (gj_rrcg *sv : b->sv) {
             sv->grid = 0;
             const gj_op *o = sv->op[0];
             if (!(o->fast && sv->prec == GJ_FP32_MIXED) || tot <= 0.0) continue;
-            const double share = (double)o->nz * (2.0 * 257 + o->ny) / tot;
-            const int g = std::max(1, (int)(sms * share));
-            if (g < o->col_grid && fast_slots(2, o->nz, g) <= o->slots && fast_slots(1, o->nz, g) <= o->slots)
+            const double share = work(o) / tot;
+            const int g = std::max(1, std::min(o->col_grid, (int)(2.0 * sms * share)));
+            const int ci = fast_col_items(o->Ny, o->nz);
+            if (g < o->col_grid && fast_slots(2, ci, g) <= o->slots && fast_slots(1, ci, g) <= o->slots)
                 sv->grid = g;
         }
     }

@@ -276,13 +276,20 @@ void make_twiddles(int N, std::vector<double> &re, std::vector<double> &im) {
 
 size_t elem_bytes(gj_precision p) { return p == GJ_FP64 ? sizeof(double) : sizeof(float); }
 
+// FP32, N_x = 512 with at most 256 prisms and stations along x, and N_y = 512 (or
+// 256) with at most 256 (128) along y.
 bool fast_eligible(const gj_op *op) {
-    return op->prec == GJ_FP32_MIXED && op->Nx == 512 && op->Ny == 512 && op->nx <= 256 && op->ny <= 256 &&
-           op->sx <= 256 && op->sy <= 256;
+    const int hy = op->Ny / 2;
+    return op->prec == GJ_FP32_MIXED && op->Nx == 512 && (op->Ny == 512 || op->Ny == 256) && op->nx <= 256 &&
+           op->sx <= 256 && op->ny <= hy && op->sy <= hy;
 }
 
+// Items per (field, kx) column of the fast column kernels: one per layer at N_y = 512,
+// one per layer pair at N_y = 256.
+int fast_col_items(int Ny, int nz) { return Ny == 256 ? (nz + 1) / 2 : nz; }
+
 // Largest number of warps that share one (field, kx) column when the persistent
-// column kernels split the (kx, field, layer) sequence into balanced segments.
+// column kernels split the (kx, field, item) sequence into balanced segments.
 int fast_slots(int nfield, int nz, int grid_ctas) {
     const long long T = (long long)nfield * 257 * nz;
     const long long Wt = std::min((long long)grid_ctas * f512::CWARPS, T);
@@ -524,7 +531,8 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         op->col_grid = std::max(1, sms);
-        op->slots = std::max(fast_slots(1, G.nz, op->col_grid), fast_slots(2, G.nz, op->col_grid));
+        const int ci = fast_col_items(Ny, G.nz);
+        op->slots = std::max(fast_slots(1, ci, op->col_grid), fast_slots(2, ci, op->col_grid));
         // gravity over a station grid that covers the prisms with no offset: the table
         // is even in both offsets, so its spectrum is real
         op->real_spec = field == GJ_GRAVITY && G.sx == G.nx && G.sy == G.ny && G.off_x == 0 && G.off_y == 0;
@@ -553,10 +561,10 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         if ((e = cudaMalloc(&op->Y, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
     } else {
-        // transposed intermediates [r][kx][256], partials [kx][slots][512], counters
-        const size_t zb = (size_t)G.nz * 257 * 256 * cs;
-        const size_t wb = (size_t)257 * 256 * cs;
-        const size_t pb = (size_t)257 * op->slots * 512 * cs;
+        // transposed intermediates [r][kx][Ny/2], partials [kx][slots][Ny], counters
+        const size_t zb = (size_t)G.nz * 257 * (Ny / 2) * cs;
+        const size_t wb = (size_t)257 * (Ny / 2) * cs;
+        const size_t pb = (size_t)257 * op->slots * Ny * cs;
         const size_t yb = pb + 257 * sizeof(int) + 64;
         op->ws_bytes = zb + wb + yb;
         if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
@@ -574,8 +582,9 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         op->err = op->cnt + 257 + 8;
         const size_t tb = (size_t)f512::TabTw<float>::WORDS * sizeof(float2);
         if ((e = cudaMalloc(&op->twtab, tb)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
+        // from the W512 table of the rows (N_x = 512 on this path, whatever N_y)
         f512::k_build_twtab<float><<<1, 256, 0, st>>>(static_cast<float2 *>(op->twtab),
-                                                    static_cast<const float2 *>(op->twy));
+                                                    static_cast<const float2 *>(op->twx));
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
     }
     *out = op;

@@ -163,6 +163,16 @@ def ragged_joint(seed: int = 6) -> Workload:
     return Workload("joint-15x13x6", g, Mag(50000.0, 60.0, 10.0), (m1, m2), (e[0], e[1]))
 
 
+def odd_joint(seed: int = 7) -> Workload:
+    """20x11 stations, 20x11x7 cubes of 50 m (an odd number of layers and of rows);
+    smooth plus blocky models."""
+    g = uniform_grid(20, 11, 20, 11, 7, 50.0)
+    m1 = smooth_blocky(g, 0.5, seed, n_boxes=3, sigma=2.0)
+    m2 = smooth_blocky(g, 0.05, seed + 1000, n_boxes=3, sigma=2.0)
+    e = standard_normal((2, g.s), seed)
+    return Workload("joint-20x11x7", g, Mag(50000.0, 60.0, 10.0), (m1, m2), (e[0], e[1]))
+
+
 def operator_128(seed: int = 2) -> Workload:
     """128x128 stations, 128x128x32 cells of 50 m; smooth plus blocky models."""
     g = uniform_grid(128, 128, 128, 128, 32, 50.0)

@@ -35,7 +35,8 @@ def run(gj, batched, iters=12):
     params = gj.solver_params(p=(1, 1), lam=(2.0, 100.0), kmax=iters, stop_on_chi2=False)
     probs, solvers, models = [], [], []
     for i, (nx, ny, nz) in enumerate(SIZES):
-        npad = (512, 512) if i == 2 else (0, 0)  # one problem on the specialised kernels
+        # one problem on each of the specialised kernels' padded sizes
+        npad = {2: (512, 512), 4: (256, 512)}.get(i, (0, 0))
         g, ops, dob, sig, wd = make_problem(gj, nx, ny, nz, 10 + i, npad)
         m = [torch.zeros(g.n, device="cuda") for _ in range(2)]
         probs.append((ops, dob, sig, wd, m))
@@ -95,7 +96,7 @@ def test_batched_problem_matches_oracle():
                          [dev(x) for x in wdep], m, history=True)]
     others = []
     for i, (nx, ny, nz) in enumerate([(24, 20, 5), (40, 40, 8)]):
-        go, opso, dobo, sigo, wdo = make_problem(gj, nx, ny, nz, 60 + i, npad=(512, 512))
+        go, opso, dobo, sigo, wdo = make_problem(gj, nx, ny, nz, 60 + i, npad=[(256, 512), (512, 512)][i])
         mo = [torch.zeros(go.n, device="cuda") for _ in range(2)]
         others.append((opso, dobo, sigo, wdo, mo))
         solvers.append(gj.Solver(opso, gj.solver_params(**kw), dobo, sigo, wdo, mo))

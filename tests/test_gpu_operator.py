@@ -36,7 +36,15 @@ CASES = {
     "fast512_small": (_grid(16, 16, 16, 16, 3), (512, 512)),
     "fast512_ragged": (_grid(13, 11, 20, 9, 2, dx=40.0, dy=55.0, off=(3, 0)), (512, 512)),
     "fast512_odd_lines": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (512, 512)),
+    # 256-row embeddings (N_y = 256, N_x = 512): the specialised kernels with
+    # half-warp column transforms over layer pairs (odd layer counts leave one half idle)
+    "fast256_small": (_grid(16, 16, 16, 16, 3), (256, 512)),
+    "fast256_ragged": (_grid(13, 11, 20, 9, 2, dx=40.0, dy=55.0, off=(3, 0)), (256, 512)),
+    "fast256_odd_lines": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (256, 512)),
+    "fast256_offset_y": (_grid(9, 12, 9, 10, 4, dx=30.0, off=(0, 2)), (256, 512)),
 }
+
+FAST = {(512, 512), (256, 512)}
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +60,7 @@ def test_products_match_dense_oracle(gj, case, field, prec):
     f = oop.GRAVITY if field == "gravity" else oop.MAGNETIC
     A = oop.dense_matrix(g, f, MAG)
     op = gj.bttb_setup(g, field, MAG if field == "magnetic" else None, precision=prec, npad=npad)
-    assert op.info.fast_path == (1 if (prec == "fp32" and npad == (512, 512)) else 0)
+    assert op.info.fast_path == (1 if (prec == "fp32" and npad in FAST) else 0)
     rng = np.random.default_rng(11)
     for trial in range(2):
         m = rng.uniform(0.0, 1.0, g.n) if trial == 0 else rng.standard_normal(g.n)
@@ -176,7 +184,7 @@ def test_joint_256_sampled_rows(gj, c3_tables, prec):
         op.close()
 
 
-@pytest.mark.parametrize("case", ["fast512_small", "fast512_ragged", "joint16"])
+@pytest.mark.parametrize("case", ["fast512_small", "fast512_ragged", "joint16", "fast256_ragged", "fast256_odd_lines"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_pair_products_match_dense_oracle(gj, case, prec):
     """gj_g_forward_pair / gj_g_adjoint_pair: both fields in one call (one set of joint
@@ -201,3 +209,46 @@ def test_pair_products_match_dense_oracle(gj, case, prec):
         assert rel(di, ds) <= tol and rel(ai, as_) <= tol
     with pytest.raises(ValueError):
         gj.g_forward_pair([ops[0], ops[0]], [to_dev(x, prec) for x in m])
+
+
+@pytest.mark.parametrize("shape", [(96, 128, 7), (128, 128, 6), (200, 100, 9)])
+def test_fast256_largest_columns_sampled_rows(gj, shape):
+    """N_y = 256 at its limits (up to 128 stations and prisms per column, odd and even
+    layer counts, 100 m cells): sampled forward rows and adjoint cells against direct
+    sums, and the same products through the 512 x 512 kernels."""
+    nx, ny, nz = shape
+    g = synth.uniform_grid(nx, ny, nx, ny, nz, 100.0)
+    rng = np.random.default_rng(12)
+    st = np.unique(np.concatenate([[0, g.s - 1, g.sx - 1, g.s - g.sx], rng.integers(0, g.s, 24)]))
+    cells = np.unique(np.concatenate([[0, g.n - 1, g.nx * g.ny - 1], rng.integers(0, g.n, 40)]))
+    m = synth.smooth_blocky(g, 1.0, seed=3)
+    r = rng.standard_normal(g.s)
+    for f, name in [(oop.GRAVITY, "gravity"), (oop.MAGNETIC, "magnetic")]:
+        K = oop.kernel_table(g, f, MAG) if f == oop.MAGNETIC else oop.kernel_table(g, f)
+        op = gj.bttb_setup(g, name, MAG if name == "magnetic" else None, precision="fp32", npad=(256, 512))
+        assert op.info.fast_path == 1 and op.info.Ny == 256
+        d = op.forward(to_dev(m, "fp32")).cpu().numpy()
+        a = op.adjoint(to_dev(r, "fp32")).cpu().numpy()
+        assert rel(d[st], oop.forward_rows(K, g, m, st)) <= TOL["fp32"], name
+        assert rel(a[cells], oop.adjoint_cols(K, g, r, cells)) <= TOL["fp32"], name
+        op512 = gj.bttb_setup(g, name, MAG if name == "magnetic" else None, precision="fp32", npad=(512, 512))
+        assert rel(d, op512.forward(to_dev(m, "fp32")).cpu().numpy()) <= 1e-6
+        assert rel(a, op512.adjoint(to_dev(r, "fp32")).cpu().numpy()) <= 1e-6
+        op.close()
+        op512.close()
+
+
+def test_fast256_needs_room_for_the_columns(gj):
+    """More than 128 stations or prisms per column keep N_y = 256 on the general
+    kernels, with the same products as the 512 x 512 kernels."""
+    m_seed = 4
+    for sy, ny in [(129, 120), (100, 129)]:
+        g = synth.uniform_grid(16, sy, 16, ny, 2, 50.0)
+        op = gj.bttb_setup(g, "gravity", precision="fp32", npad=(256, 512))
+        assert op.info.fast_path == 0
+        ref = gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512))
+        assert ref.info.fast_path == 1
+        m = synth.smooth_blocky(g, 1.0, seed=m_seed)
+        assert rel(op.forward(to_dev(m, "fp32")).cpu().numpy(), ref.forward(to_dev(m, "fp32")).cpu().numpy()) <= 1e-6
+        op.close()
+        ref.close()

@@ -141,12 +141,14 @@ def test_stepwise_graph_and_eager_match_one_shot(small, graph):
         assert rel(m2[i], m1[i]) <= 1e-12
 
 
-def test_joint_fp32_on_the_512_kernels(small):
-    """The same solve with 512 x 512 embeddings, served by the specialised kernels."""
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512)])
+def test_joint_fp32_on_the_512_kernels(small, npad):
+    """The same solve with 512 x 512 (or 256 x 512) embeddings, served by the
+    specialised kernels."""
     gj = lib()
     w, g, A, dob, sig, wdep = small
     ref = run_oracle(g, A, dob, sig, wdep, oracle_params(KW))
-    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", KW, npad=(512, 512))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", KW, npad=npad)
     assert rep["iterations"] == 50
     for i in range(2):
         assert rel(m[i], ref.m[i]) <= 1e-3, (i, rel(m[i], ref.m[i]))
@@ -168,7 +170,7 @@ def test_fast_graph_and_eager_agree(small, graph):
 
 
 @pytest.mark.parametrize("anchor", ["apriori", "previous"])
-@pytest.mark.parametrize("path", ["fp64", "fp32_512"])
+@pytest.mark.parametrize("path", ["fp64", "fp32_512", "fp32_256"])
 def test_a_priori_model_and_hard_weights(small, path, anchor):
     """m_apr in the Lp factor and the anchor (Eq. WL, RRCG:4) and W_hard in W (Eq. W),
     on the generic FP64 kernels and on the 512 x 512 FP32 kernels."""
@@ -178,7 +180,8 @@ def test_a_priori_model_and_hard_weights(small, path, anchor):
     w_hard = [synth.uniform_model(g, 0.5, 2.0, seed=23), synth.uniform_model(g, 0.5, 2.0, seed=24)]
     kw = dict(KW, kmax=20, anchor=anchor)
     ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw), m_apr=m_apr, w_hard=w_hard)
-    prec, npad, tol = ("fp64", (0, 0), 1e-8) if path == "fp64" else ("fp32", (512, 512), 1e-3)
+    prec, npad, tol = {"fp64": ("fp64", (0, 0), 1e-8), "fp32_512": ("fp32", (512, 512), 1e-3),
+                       "fp32_256": ("fp32", (256, 512), 1e-3)}[path]
     m, rep = run_gpu(gj, w, g, dob, sig, wdep, prec, kw, npad=npad, m_apr=m_apr, w_hard=w_hard)
     assert rep["iterations"] == 20
     if prec == "fp64":
@@ -196,8 +199,9 @@ def ragged():
     return (w,) + joint_case(w)
 
 
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512)])
 @pytest.mark.parametrize("optional", [False, True])
-def test_fast_solver_partial_line_groups(ragged, optional):
+def test_fast_solver_partial_line_groups(ragged, optional, npad):
     """13 rows per layer: the 512 kernels' cell-line passes, which take aligned groups
     of four rows, end every layer with a one-row group.  With and without hard
     weights, which select the kernels that read the optional rows.  (An a-priori
@@ -208,7 +212,7 @@ def test_fast_solver_partial_line_groups(ragged, optional):
     test_a_priori_model_and_hard_weights.)"""
     gj = lib()
     w, g, A, dob, sig, wdep = ragged
-    probe = gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512))
+    probe = gj.bttb_setup(g, "gravity", precision="fp32", npad=npad)
     assert probe.info.fast_path == 1
     probe.close()
     kw = dict(KW, kmax=20)
@@ -216,7 +220,34 @@ def test_fast_solver_partial_line_groups(ragged, optional):
     if optional:
         extra = dict(w_hard=[synth.uniform_model(g, 0.5, 2.0, seed=33), synth.uniform_model(g, 0.5, 2.0, seed=34)])
     ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw), **extra)
-    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=(512, 512), **extra)
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=npad, **extra)
+    assert rep["iterations"] == 20
+    for k in range(20):
+        for i in range(2):
+            assert rep["history"][k]["phi"][i] == pytest.approx(ref.history[k]["phi"][i], rel=1e-4), (k, i)
+    for i in range(2):
+        assert rel(m[i], ref.m[i]) <= 1e-4, (i, rel(m[i], ref.m[i]))
+
+
+@pytest.fixture(scope="module")
+def odd():
+    w = synth.odd_joint()
+    return (w,) + joint_case(w)
+
+
+@pytest.mark.parametrize("graph", [None, True])
+def test_fast256_solver_odd_layers(odd, graph):
+    """20x11x7 on the 256-row kernels: seven layers make the last layer pair of every
+    column half empty; Phi every iteration and the models against the FP64 oracle,
+    eager and graph-replayed."""
+    gj = lib()
+    w, g, A, dob, sig, wdep = odd
+    probe = gj.bttb_setup(g, "gravity", precision="fp32", npad=(256, 512))
+    assert probe.info.fast_path == 1
+    probe.close()
+    kw = dict(KW, kmax=20)
+    ref = run_oracle(g, A, dob, sig, wdep, oracle_params(kw))
+    m, rep = run_gpu(gj, w, g, dob, sig, wdep, "fp32", kw, npad=(256, 512), graph=graph)
     assert rep["iterations"] == 20
     for k in range(20):
         for i in range(2):

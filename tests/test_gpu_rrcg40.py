@@ -1,4 +1,4 @@
-"""Parity of the fused FP32 joint solve on the 512 x 512 kernels at the benchmark's
+"""Parity of the fused FP32 joint solve on the 512 x 512 (and 256 x 512) kernels at the benchmark's
 layer count (Eq. RRCG:1-8, Secs. 2.5, 2.6, 2.8): both fields interleaved in the
 column passes with 40-layer columns split across warps, and the team row passes.
 
@@ -31,9 +31,9 @@ def oracle_solve(fwd, adj, dob, sig, wdep, g, kmax):
     return rrcg_joint(fwd, adj, dob, sig, [np.zeros(g.n)] * 2, [np.repeat(wdep[i], g.nx * g.ny) for i in range(2)], P)
 
 
-def gpu_solve(gj, w, g, dob, sig, wdep, kmax):
-    ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=(512, 512)),
-           gj.bttb_setup(g, "magnetic", w.mag, precision="fp32", npad=(512, 512))]
+def gpu_solve(gj, w, g, dob, sig, wdep, kmax, npad=(512, 512)):
+    ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=npad),
+           gj.bttb_setup(g, "magnetic", w.mag, precision="fp32", npad=npad)]
     assert ops[0].info.fast_path == 1 and ops[1].info.fast_path == 1
     m = [to_dev(np.zeros(g.n), "fp32") for _ in range(2)]
     rep = gj.rrcg_joint_solve(ops, gj.solver_params(kmax=kmax, **KW), [to_dev(x, "fp32") for x in dob],
@@ -55,7 +55,8 @@ def check(name, ref, m, rep, kmax):
         assert m[i].min() >= np.float32(KW["lo"][i]) and m[i].max() <= np.float32(KW["hi"][i])
 
 
-def test_fast_joint_solve_40_layers_against_dense_oracle():
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512)])
+def test_fast_joint_solve_40_layers_against_dense_oracle(npad):
     gj = lib()
     w = synth.joint_256(n=32)
     g = w.grid
@@ -67,8 +68,8 @@ def test_fast_joint_solve_40_layers_against_dense_oracle():
     kmax = 25
     ref = oracle_solve([lambda x, i=i: A[i] @ x for i in range(2)], [lambda y, i=i: A[i].T @ y for i in range(2)],
                        dob, sig, wdep, g, kmax)
-    m, rep = gpu_solve(gj, w, g, dob, sig, wdep, kmax)
-    check("32x32x40", ref, m, rep, kmax)
+    m, rep = gpu_solve(gj, w, g, dob, sig, wdep, kmax, npad)
+    check(f"32x32x40 padded {npad[0]}x{npad[1]}", ref, m, rep, kmax)
 
 
 def test_fast_joint_solve_benchmark_workload_against_fft_oracle():
@@ -84,3 +85,21 @@ def test_fast_joint_solve_benchmark_workload_against_fft_oracle():
     ref = oracle_solve([B[0].forward, B[1].forward], [B[0].adjoint, B[1].adjoint], dob, sig, wdep, g, kmax)
     m, rep = gpu_solve(gj, w, g, dob, sig, wdep, kmax)
     check("256x256x40", ref, m, rep, kmax)
+
+
+def test_fast256_joint_solve_128x128x40_against_fft_oracle():
+    """The largest grid of the 256-row kernels (128 x 128 stations over 128 x 128 x 40
+    cells of 100 m, padded 256 x 512), 8 iterations against the FFT oracle at the
+    same padded size."""
+    gj = lib()
+    w = synth.joint_256(n=128)
+    g = w.grid
+    B = [oop.BCCB(oop.kernel_table(g, oop.GRAVITY), g, 256, 512),
+         oop.BCCB(oop.kernel_table(g, oop.MAGNETIC, w.mag), g, 256, 512)]
+    obs = [owt.noisy_data(B[i].forward(w.m_true[i]), 0.01, 0.01, w.noise[i]) for i in range(2)]
+    dob, sig = [o[0] for o in obs], [o[1] for o in obs]
+    wdep = [owt.depth_weights(g.z_edges, 2.0), owt.depth_weights(g.z_edges, 3.0)]
+    kmax = 8
+    ref = oracle_solve([B[0].forward, B[1].forward], [B[0].adjoint, B[1].adjoint], dob, sig, wdep, g, kmax)
+    m, rep = gpu_solve(gj, w, g, dob, sig, wdep, kmax, (256, 512))
+    check("128x128x40 padded 256x512", ref, m, rep, kmax)
