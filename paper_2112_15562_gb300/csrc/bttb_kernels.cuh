@@ -27,10 +27,15 @@ struct OpView {
     cpx<R> *Y;           // [Ny][ncol]     summed spectrum / residual spectrum
     cpx<R> *W;           // [max(sy, ...)][ncol]  inverse-column output / residual rows
     cpx<R> *V;           // fast path: residual-row spectra [ncol][256] (unused otherwise)
-    int real_spec;       // fast path: spec holds only real parts, R[nz][ncol][Ny] (even table)
+    int real_spec;       // fast path: spec holds the real, even spectrum of an even table for
+                         // ky <= Ny/2 only, R[nz][ncol][even_spec_len(Ny)]
     int rbase;           // first layer of a column launch (per-layer launches of the recompute mode)
     int spec_r0;         // layer held at spec index 0 (0 when all layers are stored)
 };
+
+// Stored entries per column of a real, even spectrum (fast path): ky = 0 .. Ny/2,
+// padded to a multiple of four values so that every column starts on 16 bytes.
+__host__ __device__ constexpr int even_spec_len(int Ny) { return Ny / 2 + 4; }
 
 // How real lines are paired into complex transforms.
 struct PairMap {

@@ -180,6 +180,13 @@ __device__ __forceinline__ int ppos(int k) { return ((k & 1) << 8) | (k >> 1); }
 // and of column kx (0 <= kx <= 256) in the inverse passes' staging tile
 __device__ __forceinline__ int kpos(int kx) { return (kx & 1) ? 129 + (kx >> 1) : (kx >> 1); }
 
+// Real, even spectra (the gravity table over stations that cover the prisms) keep
+// ky <= N/2 only: KE values per column (a multiple of four, so that columns start on
+// 16 bytes).  Spectrum index ky = lambda + 32 k1 of the 512 transform's lane layout
+// reads entry min(ky, 512 - ky), which k1 (a compile-time index) decides.
+constexpr int KE = even_spec_len(N), KEB = KE * (int)sizeof(float);  // FP32, the fast path's precision
+__device__ __forceinline__ int even_pos512(int lam, int k1) { return k1 < 8 ? lam + 32 * k1 : N - 32 * k1 - lam; }
+
 // swizzled 16 x 16 tile of one half-warp: entry (row, col) at row*16 + (col ^ row)
 __device__ __forceinline__ int swz(int row, int col) { return row * 16 + (col ^ row); }
 
@@ -414,9 +421,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
         const OpView<R> &op = V.op[ci.fld];
         const size_t off = (size_t)ci.r * NC + ci.kx;
         if (op.real_spec) {
-            mbar_expect(&bars[warp][s], ZB + TB / 2);
+            mbar_expect(&bars[warp][s], ZB + KEB);
             bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + off * N, TB / 2, &bars[warp][s]);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + off * KE, KEB, &bars[warp][s]);
         } else {
             mbar_expect(&bars[warp][s], ZB + TB);
             bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
             const R *tr = reinterpret_cast<const R *>(ts + s * N);
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
-                const R tt = tr[lam + 32 * k1];
+                const R tt = tr[even_pos512(lam, k1)];
                 acc[k1] = mk<C>(acc[k1].x + v[k1].x * tt, acc[k1].y + v[k1].y * tt);
             }
         } else {
@@ -556,8 +563,8 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
         const int s = (ti - t0) % CSTAGES;
         const size_t off = (size_t)ci.r * NC + ci.kx;
         if (V.op[ci.fld].real_spec) {
-            mbar_expect(&bars[warp][s], TB / 2);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[ci.fld].spec) + off * N, TB / 2, &bars[warp][s]);
+            mbar_expect(&bars[warp][s], KEB);
+            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[ci.fld].spec) + off * KE, KEB, &bars[warp][s]);
         } else {
             mbar_expect(&bars[warp][s], TB);
             bulk_load(ts + s * N, V.op[ci.fld].spec + off * N, TB, &bars[warp][s]);
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
             const R *tr = reinterpret_cast<const R *>(ts + s * N);
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
-                const R tt = tr[lam + 32 * k1];
+                const R tt = tr[even_pos512(lam, k1)];
                 v[k1] = mk<C>(vh[k1].x * tt, vh[k1].y * tt);
             }
         } else {
@@ -622,6 +629,9 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
 // St[r][kx][ky < 256], Wt/Vt[kx][jy < 128].
 
 constexpr int N2 = 256, H2 = 128;
+// even spectra at N_y = 256: ky <= 128 kept; index ky = l + 16 k1 reads min(ky, 256 - ky)
+constexpr int KE2 = even_spec_len(N2), KEB2 = KE2 * (int)sizeof(float);
+__device__ __forceinline__ int even_pos256(int l, int k1) { return k1 < 8 ? l + 16 * k1 : N2 - 16 * k1 - l; }
 
 // Forward pruned 256-point transform of this half-warp's column.  In: v[j] =
 // x[l + 16 j] for j < 8 (v[8..15] ignored, taken as zero).  Out: v[k1] = X[k2 + 16 k1].
@@ -701,13 +711,13 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd256(View2<R> V, const
         const OpView<R> &op = V.op[ci.fld];
         const int r0 = 2 * ci.r, nl = r0 + 1 < nz ? 2 : 1;
         const size_t off = (size_t)r0 * NC + ci.kx;
-        const uint32_t tb = op.real_spec ? TB / 2 : TB;
+        const uint32_t tb = op.real_spec ? KEB2 : TB;
         mbar_expect(&bars[warp][s], nl * (ZB + tb));
         for (int i = 0; i < nl; ++i) {
             const size_t o = off + (size_t)i * NC;
             bulk_load(zs + (s * 2 + i) * H2, op.Z + o * H2, ZB, &bars[warp][s]);
             if (op.real_spec)
-                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * N2, reinterpret_cast<const R *>(op.spec) + o * N2,
+                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * KE2, reinterpret_cast<const R *>(op.spec) + o * KE2,
                           tb, &bars[warp][s]);
             else
                 bulk_load(ts + (s * 2 + i) * N2, op.spec + o * N2, tb, &bars[warp][s]);
@@ -735,10 +745,10 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd256(View2<R> V, const
         fwd256h<R>(v, xbuf, tw);
         if (mine) {
             if (V.op[cu.fld].real_spec) {
-                const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * N2;
+                const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * KE2;
 #pragma unroll
                 for (int k1 = 0; k1 < 16; ++k1) {
-                    const R tt = tr[l + 16 * k1];
+                    const R tt = tr[even_pos256(l, k1)];
                     acc[k1] = mk<C>(acc[k1].x + v[k1].x * tt, acc[k1].y + v[k1].y * tt);
                 }
             } else {
@@ -851,12 +861,12 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj256(View2<R> V, const
         const OpView<R> &op = V.op[ci.fld];
         const int r0 = 2 * ci.r, nl = r0 + 1 < nz ? 2 : 1;
         const size_t off = (size_t)r0 * NC + ci.kx;
-        const uint32_t tb = op.real_spec ? TB / 2 : TB;
+        const uint32_t tb = op.real_spec ? KEB2 : TB;
         mbar_expect(&bars[warp][s], nl * tb);
         for (int i = 0; i < nl; ++i) {
             const size_t o = off + (size_t)i * NC;
             if (op.real_spec)
-                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * N2, reinterpret_cast<const R *>(op.spec) + o * N2,
+                bulk_load(reinterpret_cast<R *>(ts + s * 2 * N2) + i * KE2, reinterpret_cast<const R *>(op.spec) + o * KE2,
                           tb, &bars[warp][s]);
             else
                 bulk_load(ts + (s * 2 + i) * N2, op.spec + o * N2, tb, &bars[warp][s]);
@@ -888,10 +898,10 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj256(View2<R> V, const
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) v[k1] = czero<C>();
         } else if (op.real_spec) {
-            const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * N2;
+            const R *tr = reinterpret_cast<const R *>(ts + s * 2 * N2) + h * KE2;
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
-                const R tt = tr[l + 16 * k1];
+                const R tt = tr[even_pos256(l, k1)];
                 v[k1] = mk<C>(vh[k1].x * tt, vh[k1].y * tt);
             }
         } else {

@@ -199,14 +199,20 @@ __global__ void __launch_bounds__(256) k_col_spec(OpView<double> op, const doubl
     __syncthreads();
     const Cx *X = fft_lines<double, false>(buf0, buf1, op.py, C, tw, Ny);
     cpx<Rout> *Sr = spec + (size_t)r * Ny * ncol;
+    const int ke = even_spec_len(Ny);
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
         const int c = it % C, ky = it / C;
         if (c0 + c < ncol) {
-            const size_t at = transposed ? (size_t)(c0 + c) * Ny + ky : (size_t)ky * ncol + c0 + c;
-            if (real_only)  // the imaginary part is zero in exact arithmetic; keep the real part
-                reinterpret_cast<Rout *>(spec)[(size_t)r * Ny * ncol + at] = (Rout)X[it].x;
-            else
+            if (real_only) {
+                // the table is even in both offsets: the spectrum is real (its imaginary part
+                // is zero in exact arithmetic) and even in ky, so only ky <= Ny/2 is kept,
+                // as R[r][kx][ke] (fast path)
+                if (ky <= Ny / 2)
+                    reinterpret_cast<Rout *>(spec)[((size_t)r * ncol + c0 + c) * ke + ky] = (Rout)X[it].x;
+            } else {
+                const size_t at = transposed ? (size_t)(c0 + c) * Ny + ky : (size_t)ky * ncol + c0 + c;
                 Sr[at] = mk<cpx<Rout>>((Rout)X[it].x, (Rout)X[it].y);
+            }
         }
     }
 }
@@ -542,8 +548,14 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
     cudaError_t e;
     if ((rc = upload_twiddles(Nx, prec, &op->twx)) != GJ_OK) goto fail;
     if ((rc = upload_twiddles(Ny, prec, &op->twy)) != GJ_OK) goto fail;
-    op->spec_bytes = (size_t)(op->recompute ? 1 : G.nz) * Ny * op->ncol * (op->real_spec ? cs / 2 : cs);
+    op->spec_bytes = op->real_spec ? (size_t)G.nz * op->ncol * even_spec_len(Ny) * (cs / 2)
+                                   : (size_t)(op->recompute ? 1 : G.nz) * Ny * op->ncol * cs;
     if ((e = cudaMalloc(&op->spec, op->spec_bytes)) != cudaSuccess) { rc = cuda_fail(e, "spectra"); goto fail; }
+    // the even spectra's padding entries stay zero
+    if (op->real_spec && (e = cudaMemset(op->spec, 0, op->spec_bytes)) != cudaSuccess) {
+        rc = cuda_fail(e, "spectra");
+        goto fail;
+    }
     if (op->recompute) {
         // one layer's spectrum plus the build's work buffers for one layer, kept
         if ((rc = scratch_alloc(op, 1, &op->scratch)) != GJ_OK) goto fail;
