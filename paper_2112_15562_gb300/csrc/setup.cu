@@ -86,40 +86,49 @@ __constant__ double kGL3w[3] = {0.55555555555555555556, 0.88888888888888888889, 
 
 // The integral over [u1, u2] x [v1, v2] x [w1, w2] of w / R^3 (gravity) or of
 // t^T (d2(1/R)/dr dr) t = (c0 (3u^2 - R^2) + c1 (3v^2 - R^2) + c2 (3w^2 - R^2)
-// + 3 (c3 uv + c4 uw + c5 vw)) / R^5 (magnetic), by an n-point tensor rule.
-template <int NP>
-__device__ double far_cubature(double uc, double hu, double vc, double hv, double wc, double hw, int magnetic,
+// + 3 (c3 uv + c4 uw + c5 vw)) / R^5 (magnetic), by an n-point tensor rule in
+// precision F.  The integrand is smooth there and the sum has no cancellation to
+// speak of, so for an FP32 operator (whose spectra are rounded to FP32) the rule runs
+// in FP32, some 30 times the FP64 rate; FP64 operators keep FP64.
+template <typename F> __device__ __forceinline__ F rsqrt_t(F x);
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+
+template <int NP, typename F>
+__device__ double far_cubature(double uc_, double hu_, double vc_, double hv_, double wc_, double hw_, int magnetic,
                                const MagCoef &k) {
     const double *x = NP == 5 ? kGL5x : (NP == 4 ? kGL4x : kGL3x);
     const double *wt = NP == 5 ? kGL5w : (NP == 4 ? kGL4w : kGL3w);
-    double s = 0.0;
+    const F uc = (F)uc_, hu = (F)hu_, vc = (F)vc_, hv = (F)hv_, wc = (F)wc_, hw = (F)hw_;
+    const F c0 = (F)k.c[0], c1 = (F)k.c[1], c2 = (F)k.c[2], c3 = (F)k.c[3], c4 = (F)k.c[4], c5 = (F)k.c[5];
+    F s = 0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
-        const double u = uc + hu * x[a];
+        const F u = uc + hu * (F)x[a];
 #pragma unroll
         for (int b = 0; b < NP; ++b) {
-            const double v = vc + hv * x[b];
-            double sw = 0.0;
+            const F v = vc + hv * (F)x[b];
+            F sw = 0;
 #pragma unroll
             for (int c = 0; c < NP; ++c) {
-                const double w = wc + hw * x[c];
-                const double r2 = u * u + v * v + w * w;
-                const double ir = rsqrt(r2);
-                const double ir3 = ir * ir * ir;
-                double f;
+                const F w = wc + hw * (F)x[c];
+                const F r2 = u * u + v * v + w * w;
+                const F ir = rsqrt_t<F>(r2);
+                const F ir3 = ir * ir * ir;
+                F f;
                 if (magnetic) {
-                    const double q = k.c[0] * (3.0 * u * u - r2) + k.c[1] * (3.0 * v * v - r2) +
-                                     k.c[2] * (3.0 * w * w - r2) + 3.0 * (k.c[3] * u * v + k.c[4] * u * w + k.c[5] * v * w);
+                    const F q = c0 * (F(3) * u * u - r2) + c1 * (F(3) * v * v - r2) + c2 * (F(3) * w * w - r2) +
+                                F(3) * (c3 * u * v + c4 * u * w + c5 * v * w);
                     f = q * ir3 * ir * ir;
                 } else {
                     f = w * ir3;
                 }
-                sw += wt[c] * f;
+                sw += (F)wt[c] * f;
             }
-            s += wt[a] * wt[b] * sw;
+            s += (F)(wt[a] * wt[b]) * sw;
         }
     }
-    return s * hu * hv * hw;
+    return (double)s * hu_ * hv_ * hw_;
 }
 
 // Row-pass input of the setup: the circulant embedding of layer r's table,
@@ -134,7 +143,14 @@ struct LoadTable {
     double dx, dy;
     const double *zw;  // depth planes of the build's layers (relative to the stations)
     int magnetic;
+    int far32;  // far-field cubature in FP32 (FP32 operators)
     MagCoef mc;
+    template <typename F> __device__ double far(double uc, double vc, double wc, double hw, double dist,
+                                                double size) const {
+        return dist < 3.0 * kFar * size ? far_cubature<5, F>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
+             : dist < 8.0 * kFar * size ? far_cubature<4, F>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
+                                        : far_cubature<3, F>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc);
+    }
     __device__ void init() {}
     __device__ double value(int line, int j) const {
         const int r = line / Ny, iy = line % Ny;
@@ -149,16 +165,21 @@ struct LoadTable {
             const double size = fmax(fmax(dx, dy), w2 - w1);
             const double dist = sqrt(uc * uc + vc * vc + wc * wc);
             if (dist >= kFar * size) {
-                const double v = dist < 3.0 * kFar * size
-                                     ? far_cubature<5>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
-                                 : dist < 8.0 * kFar * size
-                                     ? far_cubature<4>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc)
-                                     : far_cubature<3>(uc, 0.5 * dx, vc, 0.5 * dy, wc, hw, magnetic, mc);
+                const double v = far32 ? far<float>(uc, vc, wc, hw, dist, size) : far<double>(uc, vc, wc, hw, dist, size);
                 return v * scale;
             }
         }
         const int e = b_max - (cx + off_x);
         const int f = a_max - (cy + off_y);
+        if (e < 0 || e + 1 >= nbx1 || f < 0 || f + 1 >= nby1) {
+            // outside the lattice window (it covers every offset nearer than kFar prism
+            // sizes, so this is never taken): the cubature, in FP64
+            const double uc = -(double)(cx + off_x) * dx, vc = -(double)(cy + off_y) * dy;
+            const double w1 = zw[r], w2 = zw[r + 1];
+            const double size = fmax(fmax(dx, dy), w2 - w1);
+            const double dist = sqrt(uc * uc + vc * vc + 0.25 * (w1 + w2) * (w1 + w2));
+            return far<double>(uc, vc, 0.5 * (w1 + w2), 0.5 * (w2 - w1), dist, size) * scale;
+        }
         double s = 0.0;
 #pragma unroll
         for (int dk = 0; dk < 2; ++dk)
@@ -366,6 +387,27 @@ static void scratch_free(gj_setup_scratch_impl *sc) {
     delete sc;
 }
 
+// The corner lattice serves only the prisms nearer than kFar sizes (the rest take
+// the cubature), so it spans the offsets c + off in [-W, W] of each direction that the
+// table uses, W = ceil(kFar * largest side / cell) + 1: 2W + 2 points per direction
+// at most, whatever the grid.  b_max is the largest offset in the window, nb1 the
+// lattice points (offsets b_max down to the smallest, plus one).
+struct LatticeWindow { int b_max, nbx1, a_max, nby1; };
+static LatticeWindow lattice_window(const gj_op *op) {
+    double size = std::max(op->dx, op->dy);
+    for (int k = 0; k < op->nz; ++k) size = std::max(size, op->z_edges[k + 1] - op->z_edges[k]);
+    auto one = [&](int off, int s, int n, double cell, int &hi, int &nb) {
+        const int W = (int)std::ceil(kFar * size / cell) + 1;
+        hi = std::min(off + s - 1, W);
+        const int lo = std::max(off - n + 1, -W);
+        nb = std::max(2, hi - lo + 2);
+    };
+    LatticeWindow w;
+    one(op->off_x, op->sx, op->nx, op->dx, w.b_max, w.nbx1);
+    one(op->off_y, op->sy, op->ny, op->dy, w.a_max, w.nby1);
+    return w;
+}
+
 static gj_status scratch_alloc(const gj_op *op, int layers, gj_setup_scratch_impl **out) {
     gj_setup_scratch_impl *sc = new (std::nothrow) gj_setup_scratch_impl();
     if (!sc) { set_error("setup scratch: host allocation failed"); return GJ_ERR_OOM; }
@@ -380,7 +422,8 @@ static gj_status scratch_alloc(const gj_op *op, int layers, gj_setup_scratch_imp
         if ((rc = upload_twiddles(op->Nx, GJ_FP64, &sc->twx64)) != GJ_OK) { scratch_free(sc); return rc; }
         if ((rc = upload_twiddles(op->Ny, GJ_FP64, &sc->twy64)) != GJ_OK) { scratch_free(sc); return rc; }
     }
-    const size_t plane = (size_t)(op->sx + op->nx) * (op->sy + op->ny);
+    const LatticeWindow lw = lattice_window(op);
+    const size_t plane = (size_t)lw.nbx1 * lw.nby1;
     std::vector<double> zw(op->nz + 1);
     for (int k = 0; k <= op->nz; ++k) zw[k] = op->z_edges[k] - op->station_z;
     if ((e = cudaMalloc(&sc->lat, plane * (layers + 1) * sizeof(double))) != cudaSuccess ||
@@ -403,10 +446,11 @@ template <typename Rout>
 static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r0, int count, cpx<Rout> *spec,
                          cudaStream_t st) {
     Lattice L;
-    L.b_max = op->off_x + op->sx - 1;
-    L.a_max = op->off_y + op->sy - 1;
-    L.nbx1 = op->sx + op->nx;
-    L.nby1 = op->sy + op->ny;
+    const LatticeWindow lw = lattice_window(op);
+    L.b_max = lw.b_max;
+    L.a_max = lw.a_max;
+    L.nbx1 = lw.nbx1;
+    L.nby1 = lw.nby1;
     L.nz1 = count + 1;
     L.dx = op->dx;
     L.dy = op->dy;
@@ -425,7 +469,8 @@ static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r
         // G = 6.6743e-11 m^3 kg^-1 s^-2; g/cc -> kg/m^3 (1e3); m/s^2 -> mGal (1e5)
         scale *= 6.6743e-11 * 1.0e3 * 1.0e5;
     }
-    k_corner_lattice<<<1216, 256, 0, st>>>(L, magnetic, mc, sc.lat);
+    const size_t lat_pts = (size_t)L.nbx1 * L.nby1 * L.nz1;
+    k_corner_lattice<<<(int)std::min<size_t>(1216, (lat_pts + 255) / 256), 256, 0, st>>>(L, magnetic, mc, sc.lat);
 
     OpView<double> v{};
     v.sx = op->sx; v.sy = op->sy; v.nx = op->nx; v.ny = op->ny; v.nz = count;
@@ -441,6 +486,7 @@ static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r
     lt.dx = op->dx; lt.dy = op->dy;
     lt.zw = sc.zw + r0;
     lt.magnetic = magnetic;
+    lt.far32 = op->prec == GJ_FP32_MIXED ? 1 : 0;
     lt.mc = mc;
     PairMap pm{count * op->Ny, 0};
     const int P = pick_row_pairs(op->Nx, sizeof(double2));
