@@ -128,7 +128,7 @@ def tune_full(grid, mag, precision: str = "fp32", cache: Optional[str] = None, r
         ops = _setup(grid, mag, precision, cand)
         t = _time_ops(ops, reps)
         timings[f"{cand[0]}x{cand[1]}"] = t
-        if not ops[0].info.fast_path and (best_generic is None or t < best_generic[1]):
+        if ops[0].info.fast_path != 1 and (best_generic is None or t < best_generic[1]):
             best_generic = (cand, t)
         for op in ops:
             op.close()

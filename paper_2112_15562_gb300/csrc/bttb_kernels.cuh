@@ -31,6 +31,8 @@ struct OpView {
                          // ky <= Ny/2 only, R[nz][ncol][even_spec_len(Ny)]
     int rbase;           // first layer of a column launch (per-layer launches of the recompute mode)
     int spec_r0;         // layer held at spec index 0 (0 when all layers are stored)
+    int tcol;            // 0: Z, W, V row-major ([line][ncol]); > 0: transposed, line iy of layer r and
+                         // bin k at ((r * ncol + k) * tcol + iy) (the N_y = 1024 column kernels' layout)
 };
 
 // Stored entries per column of a real, even spectrum (fast path): ky = 0 .. Ny/2,
@@ -41,10 +43,18 @@ __host__ __device__ constexpr int even_spec_len(int Ny) { return Ny / 2 + 4; }
 struct PairMap {
     int nlines;  // lines per side
     int joint;   // 1: pair q = (line q of op0, line q of op1); 0: lines (2q, 2q+1) of op0
+    int lpl;     // lines per layer (0: one layer), for the transposed layout
     __device__ __forceinline__ int npairs() const { return joint ? nlines : (nlines + 1) >> 1; }
     __device__ __forceinline__ void lines(int q, int &la, int &lb, bool &hasb) const {
         if (joint) { la = q; lb = q; hasb = true; }
         else { la = 2 * q; lb = 2 * q + 1; hasb = lb < nlines; }
+    }
+    // element (line, bin k) of a row pass's output or input
+    __device__ __forceinline__ size_t at(int line, int k, int ncol, int tcol) const {
+        if (!tcol) return (size_t)line * ncol + k;
+        const int L = lpl > 0 ? lpl : nlines;
+        const int r = line / L;
+        return ((size_t)r * ncol + k) * tcol + (line - r * L);
     }
 };
 
@@ -89,8 +99,8 @@ __global__ void __launch_bounds__(256) k_row_fwd(OpView<R> op, PairMap pm, int n
         const C zm = X[((N - k) % N) * P + p];
         int la, lb; bool hb;
         pm.lines(q, la, lb, hb);
-        out0[(size_t)la * ncol + k] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-        if (hb) out1[(size_t)lb * ncol + k] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        out0[pm.at(la, k, ncol, op.tcol)] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+        if (hb) out1[pm.at(lb, k, ncol, op.tcol)] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
     }
     pro.flush(red);
 }
@@ -121,8 +131,8 @@ __global__ void __launch_bounds__(256) k_row_inv(OpView<R> op, PairMap pm, int n
             pm.lines(q, la, lb, hb);
             const bool lo = k < ncol;
             const int kk = lo ? k : N - k;
-            C A = in0[(size_t)la * ncol + kk];
-            C B = hb ? in1[(size_t)lb * ncol + kk] : czero<C>();
+            C A = in0[pm.at(la, kk, ncol, op.tcol)];
+            C B = hb ? in1[pm.at(lb, kk, ncol, op.tcol)] : czero<C>();
             if (kk == 0 || 2 * kk == N) { A.y = 0; B.y = 0; }
             z = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
         }

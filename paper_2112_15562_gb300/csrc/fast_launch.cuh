@@ -1,5 +1,6 @@
 // Host-side launch helpers of the fast path (N_x = 512; N_y = 512 or 256).
 #pragma once
+#include "fast1024.cuh"
 #include "fast512_rows.cuh"
 #include "view.cuh"
 
@@ -112,4 +113,24 @@ inline void col_adj(const View2<R> &V, int grid, const int *done, cudaStream_t s
 }
 
 }  // namespace f512
+
+namespace f1024 {
+
+template <typename R>
+inline void set_col_attr() {
+    allow_max_smem(k_col_fwd1024<R>);
+    allow_max_smem(k_col_adj1024<R>);
+}
+
+template <typename R>
+inline void col_fwd(const f512::View2<R> &V, int grid, const int *done, cudaStream_t st) {
+    k_col_fwd1024<R><<<grid, CWF * 32, smem_col_fwd<R>(), st>>>(V, done);
+}
+
+template <typename R>
+inline void col_adj(const f512::View2<R> &V, int grid, const int *done, cudaStream_t st) {
+    k_col_adj1024<R><<<grid, CWA * 32, smem_col_adj<R>(), st>>>(V, done);
+}
+
+}  // namespace f1024
 }  // namespace gj

@@ -36,7 +36,11 @@ struct gj_op {
     void *P = nullptr;     // [ncol][slots][Ny] complex
     int *cnt = nullptr;    // [ncol] arrival counters
     int *err = nullptr;    // device error word (bounded waits)
-    void *twtab = nullptr; // the column kernels' twiddle table (FP32, TabTw layout)
+    void *twtab = nullptr; // the column kernels' twiddle table (FP32, TabTw or Tab1024 layout)
+    // N_y = 1024 (FP32, at most 512 prisms and stations per column): warp-FFT column
+    // kernels with the general row kernels writing and reading transposed Z, W, V;
+    // spectra, partials, counters and the error word as on the fast path
+    bool fast1024 = false;
     // per-layer spectrum recomputation (GJ_SETUP_RECOMPUTE_SPECTRA): `spec` holds one
     // layer, rebuilt from the closed forms before each use
     bool recompute = false;
@@ -64,7 +68,9 @@ template <typename R> OpView<R> view_of(const gj_op *op);
 // fast-path helpers (setup.cu)
 bool fast_eligible(const gj_op *op);
 int fast_col_items(int Ny, int nz);  // items per column of the fast column kernels
-int fast_slots(int nfield, int items_per_col, int grid_ctas);
+// partial slots per column for persistent column kernels of `warps` warps in total
+int fast_slots(int nfield, int ncol, int items_per_col, long long warps);
+bool fast1024_eligible(const gj_op *op);
 
 // rebuilds layer r's spectrum into spec (recompute mode; setup.cu)
 void recompute_layer(const gj_op *op, int r, cudaStream_t st);

@@ -47,6 +47,73 @@ static void launch_forward(const gj_op *o, const R *m, R *d, cudaStream_t st) {
                                                                      StorePlain<R>{d, d, o->sx}, nullptr);
 }
 
+// N_y = 1024 column kernels: the general row kernels write and read the transposed
+// intermediates (PairMap.lpl gives the lines per layer); a pair call shares the column
+// launch of both fields.
+static void fast1024_forward(const gj_op *a, const gj_op *b, const float *m0, const float *m1, float *d0, float *d1,
+                             cudaStream_t st) {
+    using R = float;
+    const size_t cs = sizeof(cpx<R>);
+    const int P = a->P_row;
+    const size_t rsm = row_smem(a->Nx, P, cs);
+    allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
+    allow_max_smem(k_row_inv<R, StorePlain<R>>);
+    f1024::set_col_attr<R>();
+    const gj_op *ops[2] = {a, b};
+    const float *ms[2] = {m0, m1};
+    float *ds[2] = {d0, d1};
+    const int nf = b ? 2 : 1;
+    for (int i = 0; i < nf; ++i) {
+        const gj_op *o = ops[i];
+        OpView<R> v = view_of<R>(o);
+        PairMap pm{o->nz * o->ny, 0, o->ny};
+        const int npr = (pm.nlines + 1) / 2;
+        k_row_fwd<R, LoadPlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
+                                                                        LoadPlain<R>{ms[i], ms[i], o->nx}, nullptr);
+    }
+    f1024::col_fwd<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
+    for (int i = 0; i < nf; ++i) {
+        const gj_op *o = ops[i];
+        OpView<R> v = view_of<R>(o);
+        PairMap ps{o->sy, 0, o->sy};
+        const int nps = (ps.nlines + 1) / 2;
+        k_row_inv<R, StorePlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
+                                                                         StorePlain<R>{ds[i], ds[i], o->sx}, nullptr);
+    }
+}
+
+static void fast1024_adjoint(const gj_op *a, const gj_op *b, const float *r0, const float *r1, float *g0, float *g1,
+                             cudaStream_t st) {
+    using R = float;
+    const size_t cs = sizeof(cpx<R>);
+    const int P = a->P_row;
+    const size_t rsm = row_smem(a->Nx, P, cs);
+    allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
+    allow_max_smem(k_row_inv<R, StorePlain<R>>);
+    f1024::set_col_attr<R>();
+    const gj_op *ops[2] = {a, b};
+    const float *rs[2] = {r0, r1};
+    float *gs[2] = {g0, g1};
+    const int nf = b ? 2 : 1;
+    for (int i = 0; i < nf; ++i) {
+        const gj_op *o = ops[i];
+        OpView<R> v = view_of<R>(o);
+        PairMap ps{o->sy, 0, o->sy};
+        const int nps = (ps.nlines + 1) / 2;
+        k_row_fwd<R, LoadPlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.V, v.V,
+                                                                        LoadPlain<R>{rs[i], rs[i], o->sx}, nullptr);
+    }
+    f1024::col_adj<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
+    for (int i = 0; i < nf; ++i) {
+        const gj_op *o = ops[i];
+        OpView<R> v = view_of<R>(o);
+        PairMap pm{o->nz * o->ny, 0, o->ny};
+        const int npr = (pm.nlines + 1) / 2;
+        k_row_inv<R, StorePlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
+                                                                         StorePlain<R>{gs[i], gs[i], o->nx}, nullptr);
+    }
+}
+
 template <typename R>
 static void launch_adjoint(const gj_op *o, const R *r, R *g, cudaStream_t st) {
     OpView<R> v = view_of<R>(o);
@@ -146,12 +213,14 @@ static void fast_adjoint_pair(const gj_op *a, const gj_op *b, const float *r0, c
 // Two operators serve one joint launch when both are on the fast path with the same
 // grid (their workspaces stay separate; the launch uses the first one's error word).
 static bool pair_eligible(const gj_op *a, const gj_op *b) {
-    return a != b && a->fast && b->fast && a->sx == b->sx && a->sy == b->sy && a->nx == b->nx && a->ny == b->ny &&
-           a->nz == b->nz && a->Ny == b->Ny && a->col_grid == b->col_grid;
+    return a != b && ((a->fast && b->fast) || (a->fast1024 && b->fast1024)) && a->sx == b->sx && a->sy == b->sy &&
+           a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->Ny == b->Ny && a->Nx == b->Nx &&
+           a->P_row == b->P_row && a->col_grid == b->col_grid;
 }
 
 gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t st) {
     if (o->fast) fast_forward(o, (const float *)m, (float *)d, st);
+    else if (o->fast1024) fast1024_forward(o, nullptr, (const float *)m, nullptr, (float *)d, nullptr, st);
     else if (o->prec == GJ_FP64) launch_forward<double>(o, (const double *)m, (double *)d, st);
     else launch_forward<float>(o, (const float *)m, (float *)d, st);
     cudaError_t e = cudaGetLastError();
@@ -160,6 +229,7 @@ gj_status forward_enqueue(const gj_op *o, const void *m, void *d, cudaStream_t s
 
 gj_status adjoint_enqueue(const gj_op *o, const void *r, void *g, cudaStream_t st) {
     if (o->fast) fast_adjoint(o, (const float *)r, (float *)g, st);
+    else if (o->fast1024) fast1024_adjoint(o, nullptr, (const float *)r, nullptr, (float *)g, nullptr, st);
     else if (o->prec == GJ_FP64) launch_adjoint<double>(o, (const double *)r, (double *)g, st);
     else launch_adjoint<float>(o, (const float *)r, (float *)g, st);
     cudaError_t e = cudaGetLastError();
@@ -200,7 +270,7 @@ extern "C" gj_status gj_op_status(gj_op *op, int reset, gj_stream_t stream) {
     if (e == 0) return GJ_OK;
     if (reset) {
         // the counters of a column whose warps gave up may be nonzero: restart them
-        GJ_CUDA(cudaMemsetAsync(op->cnt, 0, 257 * sizeof(int), st));
+        GJ_CUDA(cudaMemsetAsync(op->cnt, 0, op->ncol * sizeof(int), st));
         GJ_CUDA(cudaMemsetAsync(op->err, 0, sizeof(int), st));
         GJ_CUDA(cudaStreamSynchronize(st));
     }
@@ -237,7 +307,10 @@ extern "C" gj_status gj_g_forward_pair(const gj_op *const ops[2], const void *co
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (gj::pair_eligible(ops[0], ops[1])) {
-        gj::fast_forward_pair(ops[0], ops[1], (const float *)m[0], (const float *)m[1], (float *)d[0], (float *)d[1], st);
+        if (ops[0]->fast1024)
+            gj::fast1024_forward(ops[0], ops[1], (const float *)m[0], (const float *)m[1], (float *)d[0], (float *)d[1], st);
+        else
+            gj::fast_forward_pair(ops[0], ops[1], (const float *)m[0], (const float *)m[1], (float *)d[0], (float *)d[1], st);
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? GJ_OK : gj::cuda_fail(e, "gj_g_forward_pair launch");
     }
@@ -253,7 +326,10 @@ extern "C" gj_status gj_g_adjoint_pair(const gj_op *const ops[2], const void *co
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (gj::pair_eligible(ops[0], ops[1])) {
-        gj::fast_adjoint_pair(ops[0], ops[1], (const float *)r[0], (const float *)r[1], (float *)g[0], (float *)g[1], st);
+        if (ops[0]->fast1024)
+            gj::fast1024_adjoint(ops[0], ops[1], (const float *)r[0], (const float *)r[1], (float *)g[0], (float *)g[1], st);
+        else
+            gj::fast_adjoint_pair(ops[0], ops[1], (const float *)r[0], (const float *)r[1], (float *)g[0], (float *)g[1], st);
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? GJ_OK : gj::cuda_fail(e, "gj_g_adjoint_pair launch");
     }

@@ -694,6 +694,7 @@ struct SolverLaunch {
     OpView<R> v0, v1;
     f512::View2<R> V2;
     bool fast = false;
+    bool fast1024 = false;  // general row kernels (transposed intermediates) + N_y = 1024 column kernels
     FieldVecs<R> F;
     int P, C, L;
     int grid;  // CTAs of the persistent fast-path launches
@@ -707,7 +708,8 @@ struct SolverLaunch {
         v1 = view_of<R>(sv->op[1]);
         if constexpr (std::is_same_v<R, float>) {
             fast = o->fast && sv->op[1]->fast;
-            if (fast) V2 = f512::make_view2<R>(sv->op[0], sv->op[1]);
+            fast1024 = o->fast1024 && sv->op[1]->fast1024;
+            if (fast || fast1024) V2 = f512::make_view2<R>(sv->op[0], sv->op[1]);
         }
         const size_t cs = sizeof(cpx<R>);
         P = o->P_row; C = o->C_col; L = o->L_grp;
@@ -758,6 +760,7 @@ struct SolverLaunch {
             set_col_attr<R>();
             return;
         }
+        if constexpr (std::is_same_v<R, float>) if (fast1024) f1024::set_col_attr<R>();
         allow_max_smem(k_row_fwd<R, ProModel<R>>);
         allow_max_smem(k_row_fwd<R, ProDirection<R>>);
         allow_max_smem(k_row_fwd<R, LoadPair<R>>);
@@ -785,6 +788,19 @@ struct SolverLaunch {
             if (sv->profile && sv->capturing) {
                 cut_segment(sv, st);
             } else if (sv->profile) {
+                cudaEventRecord(pp.b, st);
+                sv->eager_pairs.push_back(pp);
+            }
+            return;
+        }
+        if constexpr (std::is_same_v<R, float>) if (fast1024) {
+            ProfilePair pp{};
+            if (sv->profile && !sv->capturing) {
+                pp = take_pair(sv);
+                cudaEventRecord(pp.a, st);
+            }
+            f1024::col_fwd<R>(V2, grid, &sv->S->done, st);
+            if (sv->profile && !sv->capturing) {
                 cudaEventRecord(pp.b, st);
                 sv->eager_pairs.push_back(pp);
             }
@@ -826,11 +842,11 @@ struct SolverLaunch {
             k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
             return;
         }
-        PairMap pc{o->nz * o->ny, 1};
+        PairMap pc{o->nz * o->ny, 1, o->ny};
         ProModel<R> pm{F, sv->S, o->nx, o->ny};
         k_row_fwd<R, ProModel<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pm, done);
         forward_columns(st);
-        PairMap ps{o->sy, 1};
+        PairMap ps{o->sy, 1, o->sy};
         EpiResidual<R> er{F, sv->S, o->sx};
         k_row_inv<R, EpiResidual<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, er, done);
         k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
@@ -861,13 +877,23 @@ struct SolverLaunch {
             return;
         }
         const int nt = (o->ncol + C - 1) / C;
-        PairMap ps{o->sy, 1};
-        PairMap pc{o->nz * o->ny, 1};
+        PairMap ps{o->sy, 1, o->sy};
+        PairMap pc{o->nz * o->ny, 1, o->ny};
         // adjoint: rows of v -> W, columns -> Y, per-layer conj-spectrum columns -> Z
+        // (N_y = 1024 column kernels: rows of v -> V, then one persistent column pass)
         LoadPair<R> lv{F.v[0], F.v[1], o->sx};
-        k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, lv, done);
-        k_col_fft<R><<<dim3(nt, 2), 256, csm, st>>>(v0, v1, C, done);
-        k_col_adj<R><<<dim3(nt, o->nz, 2), 256, csm, st>>>(v0, v1, C, done);
+        bool cols1024 = false;
+        if constexpr (std::is_same_v<R, float>) cols1024 = fast1024;
+        if (cols1024) {
+            k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.V, v1.V, lv,
+                                                                                done);
+            if constexpr (std::is_same_v<R, float>) f1024::col_adj<R>(V2, grid, done, st);
+        } else {
+            k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, lv,
+                                                                                done);
+            k_col_fft<R><<<dim3(nt, 2), 256, csm, st>>>(v0, v1, C, done);
+            k_col_adj<R><<<dim3(nt, o->nz, 2), 256, csm, st>>>(v0, v1, C, done);
+        }
         EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
         k_row_inv<R, EpiGradient<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, eg, done);
         // direction and its forward product
@@ -1247,7 +1273,8 @@ extern "C" gj_status gj_rrcg_batch_create(gj_rrcg *const *solvers, int count, gj
             const double share = work(o) / tot;
             const int g = std::max(1, std::min(o->col_grid, (int)(2.0 * sms * share)));
             const int ci = fast_col_items(o->Ny, o->nz);
-            if (g < o->col_grid && fast_slots(2, ci, g) <= o->slots && fast_slots(1, ci, g) <= o->slots)
+            const long long warps = (long long)g * f512::CWARPS;
+            if (g < o->col_grid && fast_slots(2, 257, ci, warps) <= o->slots && fast_slots(1, 257, ci, warps) <= o->slots)
                 sv->grid = g;
         }
     }

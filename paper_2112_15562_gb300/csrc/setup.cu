@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 
+#include "fast1024.cuh"
 #include "fast512.cuh"
 #include "view.cuh"
 
@@ -315,16 +316,20 @@ bool fast_eligible(const gj_op *op) {
 // one per layer pair at N_y = 256.
 int fast_col_items(int Ny, int nz) { return Ny == 256 ? (nz + 1) / 2 : nz; }
 
-// Largest number of warps that share one (field, kx) column when the persistent
-// column kernels split the (kx, field, item) sequence into balanced segments.
-int fast_slots(int nfield, int nz, int grid_ctas) {
-    const long long T = (long long)nfield * 257 * nz;
-    const long long Wt = std::min((long long)grid_ctas * f512::CWARPS, T);
+// Largest number of warps that share one (field, kx) column when persistent column
+// kernels of `warps` warps split the (kx, field, item) sequence into balanced segments.
+int fast_slots(int nfield, int ncol, int nz, long long warps) {
+    const long long T = (long long)nfield * ncol * nz;
+    const long long Wt = std::min(warps, T);
     auto owner = [&](long long t) { return ((t + 1) * Wt + T - 1) / T - 1; };
     long long mx = 1;
-    for (long long c = 0; c < (long long)nfield * 257; ++c)
+    for (long long c = 0; c < (long long)nfield * ncol; ++c)
         mx = std::max(mx, owner(c * nz + nz - 1) - owner(c * nz) + 1);
     return (int)mx;
+}
+
+bool fast1024_eligible(const gj_op *op) {
+    return op->prec == GJ_FP32_MIXED && !op->fast && op->Ny == 1024 && op->ny <= 512 && op->sy <= 512;
 }
 
 int pick_row_pairs(int Nx, size_t cs) {
@@ -496,7 +501,7 @@ static void build_layers(const gj_op *op, const gj_setup_scratch_impl &sc, int r
     const int C = pick_col_tile(op->Ny, sizeof(double2), 2);
     const size_t csm = col_smem(op->Ny, C, 2, sizeof(double2));
     dim3 g((op->ncol + C - 1) / C, count);
-    k_col_spec<Rout><<<g, 256, csm, st>>>(v, sc.Zs, spec, C, op->fast ? 1 : 0, op->real_spec ? 1 : 0);
+    k_col_spec<Rout><<<g, 256, csm, st>>>(v, sc.Zs, spec, C, (op->fast || op->fast1024) ? 1 : 0, op->real_spec ? 1 : 0);
 }
 
 static void set_build_attributes() {
@@ -584,9 +589,20 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         op->col_grid = std::max(1, sms);
         const int ci = fast_col_items(Ny, G.nz);
-        op->slots = std::max(fast_slots(1, ci, op->col_grid), fast_slots(2, ci, op->col_grid));
+        const long long warps = (long long)op->col_grid * f512::CWARPS;
+        op->slots = std::max(fast_slots(1, 257, ci, warps), fast_slots(2, 257, ci, warps));
         // gravity over a station grid that covers the prisms with no offset: the table
         // is even in both offsets, so its spectrum is real
+        op->real_spec = field == GJ_GRAVITY && G.sx == G.nx && G.sy == G.ny && G.off_x == 0 && G.off_y == 0;
+    }
+    op->fast1024 = !op->recompute && fast1024_eligible(op);
+    if (op->fast1024) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        op->col_grid = std::max(1, sms);
+        const long long warps = (long long)op->col_grid * f1024::CWF;
+        op->slots = std::max(fast_slots(1, op->ncol, G.nz, warps), fast_slots(2, op->ncol, G.nz, warps));
         op->real_spec = field == GJ_GRAVITY && G.sx == G.nx && G.sy == G.ny && G.off_x == 0 && G.off_y == 0;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -610,7 +626,7 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         rc = (prec == GJ_FP64) ? build_spectra<double>(op, st) : build_spectra<float>(op, st);
         if (rc != GJ_OK) goto fail;
     }
-    if (!op->fast) {
+    if (!op->fast && !op->fast1024) {
         const size_t zb = (size_t)G.nz * G.ny * op->ncol * cs;
         const size_t yb = (size_t)Ny * op->ncol * cs;
         const size_t wb = (size_t)std::max(G.sy, 1) * op->ncol * cs;
@@ -620,10 +636,10 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
     } else {
         // transposed intermediates [r][kx][Ny/2], partials [kx][slots][Ny], counters
-        const size_t zb = (size_t)G.nz * 257 * (Ny / 2) * cs;
-        const size_t wb = (size_t)257 * (Ny / 2) * cs;
-        const size_t pb = (size_t)257 * op->slots * Ny * cs;
-        const size_t yb = pb + 257 * sizeof(int) + 64;
+        const size_t zb = (size_t)G.nz * op->ncol * (Ny / 2) * cs;
+        const size_t wb = (size_t)op->ncol * (Ny / 2) * cs;
+        const size_t pb = (size_t)op->ncol * op->slots * Ny * cs;
+        const size_t yb = pb + op->ncol * sizeof(int) + 64;
         op->ws_bytes = zb + wb + yb;
         if ((e = cudaMalloc(&op->Z, zb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         if ((e = cudaMalloc(&op->W, wb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
@@ -637,12 +653,15 @@ extern "C" gj_status gj_bttb_setup_ex(const gj_grid *grid, gj_field field, const
         if ((e = cudaMemset(op->Y, 0, yb)) != cudaSuccess) { rc = cuda_fail(e, "workspace"); goto fail; }
         op->P = op->Y;
         op->cnt = reinterpret_cast<int *>(static_cast<char *>(op->Y) + pb);
-        op->err = op->cnt + 257 + 8;
-        const size_t tb = (size_t)f512::TabTw<float>::WORDS * sizeof(float2);
+        op->err = op->cnt + op->ncol + 8;
+        const size_t tb = (size_t)(op->fast ? f512::TabTw<float>::WORDS : f1024::Tab1024<float>::WORDS) * sizeof(float2);
         if ((e = cudaMalloc(&op->twtab, tb)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
-        // from the W512 table of the rows (N_x = 512 on this path, whatever N_y)
-        f512::k_build_twtab<float><<<1, 256, 0, st>>>(static_cast<float2 *>(op->twtab),
-                                                    static_cast<const float2 *>(op->twx));
+        if (op->fast)  // from the W512 table of the rows (N_x = 512 on this path, whatever N_y)
+            f512::k_build_twtab<float><<<1, 256, 0, st>>>(static_cast<float2 *>(op->twtab),
+                                                        static_cast<const float2 *>(op->twx));
+        else  // from the W1024 table of the columns
+            f1024::k_build_tab1024<float><<<1, 256, 0, st>>>(static_cast<float2 *>(op->twtab),
+                                                           static_cast<const float2 *>(op->twy));
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "twiddle table"); goto fail; }
     }
     *out = op;
@@ -692,7 +711,7 @@ extern "C" gj_status gj_op_info(const gj_op *op, gj_op_info_t *info) {
     info->field = op->field; info->precision = op->prec;
     info->spectrum_bytes = (int64_t)op->spec_bytes;
     info->workspace_bytes = (int64_t)op->ws_bytes;
-    info->fast_path = op->fast ? 1 : 0;
+    info->fast_path = op->fast ? 1 : (op->fast1024 ? 2 : 0);
     info->P_row = op->P_row; info->C_col = op->C_col; info->L_grp = op->L_grp;
     info->radix_order = op->radix_order;
     info->recompute = op->recompute ? 1 : 0;

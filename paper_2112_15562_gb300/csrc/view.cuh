@@ -21,6 +21,7 @@ inline OpView<R> view_of(const gj_op *op) {
     v.real_spec = op->real_spec ? 1 : 0;
     v.rbase = 0;
     v.spec_r0 = 0;
+    v.tcol = op->fast1024 ? op->Ny / 2 : 0;
     return v;
 }
 

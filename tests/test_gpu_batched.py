@@ -36,7 +36,7 @@ def run(gj, batched, iters=12):
     probs, solvers, models = [], [], []
     for i, (nx, ny, nz) in enumerate(SIZES):
         # one problem on each of the specialised kernels' padded sizes
-        npad = {2: (512, 512), 4: (256, 512)}.get(i, (0, 0))
+        npad = {1: (1024, 24), 2: (512, 512), 4: (256, 512)}.get(i, (0, 0))
         g, ops, dob, sig, wd = make_problem(gj, nx, ny, nz, 10 + i, npad)
         m = [torch.zeros(g.n, device="cuda") for _ in range(2)]
         probs.append((ops, dob, sig, wd, m))

@@ -42,9 +42,21 @@ CASES = {
     "fast256_ragged": (_grid(13, 11, 20, 9, 2, dx=40.0, dy=55.0, off=(3, 0)), (256, 512)),
     "fast256_odd_lines": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (256, 512)),
     "fast256_offset_y": (_grid(9, 12, 9, 10, 4, dx=30.0, off=(0, 2)), (256, 512)),
+    # N_y = 1024: the warp-FFT column kernels behind the general row kernels (any N_x)
+    "cols1024_small": (_grid(16, 16, 16, 16, 3), (1024, 32)),
+    "cols1024_ragged": (_grid(13, 11, 20, 9, 2, dx=40.0, dy=55.0, off=(3, 0)), (1024, 36)),
+    "cols1024_odd_lines": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (1024, 15)),
+    "cols1024_wide": (_grid(30, 6, 24, 6, 2, dx=20.0), (1024, 1024)),
 }
 
 FAST = {(512, 512), (256, 512)}
+
+
+def fast_kind(prec, npad):
+    """gj_op_info_t.fast_path expected for a padded size."""
+    if prec != "fp32":
+        return 0
+    return 1 if npad in FAST else (2 if npad[0] == 1024 else 0)
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +72,7 @@ def test_products_match_dense_oracle(gj, case, field, prec):
     f = oop.GRAVITY if field == "gravity" else oop.MAGNETIC
     A = oop.dense_matrix(g, f, MAG)
     op = gj.bttb_setup(g, field, MAG if field == "magnetic" else None, precision=prec, npad=npad)
-    assert op.info.fast_path == (1 if (prec == "fp32" and npad in FAST) else 0)
+    assert op.info.fast_path == fast_kind(prec, npad)
     rng = np.random.default_rng(11)
     for trial in range(2):
         m = rng.uniform(0.0, 1.0, g.n) if trial == 0 else rng.standard_normal(g.n)
@@ -184,7 +196,8 @@ def test_joint_256_sampled_rows(gj, c3_tables, prec):
         op.close()
 
 
-@pytest.mark.parametrize("case", ["fast512_small", "fast512_ragged", "joint16", "fast256_ragged", "fast256_odd_lines"])
+@pytest.mark.parametrize("case", ["fast512_small", "fast512_ragged", "joint16", "fast256_ragged", "fast256_odd_lines",
+                                  "cols1024_ragged", "cols1024_odd_lines"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_pair_products_match_dense_oracle(gj, case, prec):
     """gj_g_forward_pair / gj_g_adjoint_pair: both fields in one call (one set of joint
@@ -252,3 +265,30 @@ def test_fast256_needs_room_for_the_columns(gj):
         assert rel(op.forward(to_dev(m, "fp32")).cpu().numpy(), ref.forward(to_dev(m, "fp32")).cpu().numpy()) <= 1e-6
         op.close()
         ref.close()
+
+
+@pytest.mark.parametrize("shape", [(96, 512, 5), (512, 64, 3), (300, 260, 4)])
+def test_cols1024_largest_columns_sampled_rows(gj, shape):
+    """N_y = 1024 at its limits (up to 512 stations and prisms per column, 100 m cells):
+    sampled forward rows and adjoint cells against direct sums, FP32 against FP64."""
+    nx, ny, nz = shape
+    g = synth.uniform_grid(nx, ny, nx, ny, nz, 100.0)
+    rng = np.random.default_rng(13)
+    st = np.unique(np.concatenate([[0, g.s - 1, g.sx - 1, g.s - g.sx], rng.integers(0, g.s, 24)]))
+    cells = np.unique(np.concatenate([[0, g.n - 1, g.nx * g.ny - 1], rng.integers(0, g.n, 40)]))
+    m = synth.uniform_model(g, 0.0, 1.0, seed=3)
+    r = rng.standard_normal(g.s)
+    Nx = {96: 192, 512: 1024, 300: 600}[nx]
+    for f, name in [(oop.GRAVITY, "gravity"), (oop.MAGNETIC, "magnetic")]:
+        K = oop.kernel_table(g, f, MAG) if f == oop.MAGNETIC else oop.kernel_table(g, f)
+        op = gj.bttb_setup(g, name, MAG if name == "magnetic" else None, precision="fp32", npad=(1024, Nx))
+        assert op.info.fast_path == 2 and op.info.Ny == 1024
+        d = op.forward(to_dev(m, "fp32")).cpu().numpy()
+        a = op.adjoint(to_dev(r, "fp32")).cpu().numpy()
+        assert rel(d[st], oop.forward_rows(K, g, m, st)) <= TOL["fp32"], name
+        assert rel(a[cells], oop.adjoint_cols(K, g, r, cells)) <= TOL["fp32"], name
+        op64 = gj.bttb_setup(g, name, MAG if name == "magnetic" else None, precision="fp64", npad=(1024, Nx))
+        assert rel(d, op64.forward(to_dev(m, "fp64")).cpu().numpy()) <= 1e-6
+        assert rel(a, op64.adjoint(to_dev(r, "fp64")).cpu().numpy()) <= 1e-6
+        op.close()
+        op64.close()

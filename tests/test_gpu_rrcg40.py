@@ -34,7 +34,8 @@ def oracle_solve(fwd, adj, dob, sig, wdep, g, kmax):
 def gpu_solve(gj, w, g, dob, sig, wdep, kmax, npad=(512, 512)):
     ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=npad),
            gj.bttb_setup(g, "magnetic", w.mag, precision="fp32", npad=npad)]
-    assert ops[0].info.fast_path == 1 and ops[1].info.fast_path == 1
+    kind = 2 if npad[0] == 1024 else 1
+    assert ops[0].info.fast_path == kind and ops[1].info.fast_path == kind
     m = [to_dev(np.zeros(g.n), "fp32") for _ in range(2)]
     rep = gj.rrcg_joint_solve(ops, gj.solver_params(kmax=kmax, **KW), [to_dev(x, "fp32") for x in dob],
                               [to_dev(x, "fp32") for x in sig], [to_dev(x, "fp32") for x in wdep], m, history=True)
@@ -55,7 +56,7 @@ def check(name, ref, m, rep, kmax):
         assert m[i].min() >= np.float32(KW["lo"][i]) and m[i].max() <= np.float32(KW["hi"][i])
 
 
-@pytest.mark.parametrize("npad", [(512, 512), (256, 512)])
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 64)])
 def test_fast_joint_solve_40_layers_against_dense_oracle(npad):
     gj = lib()
     w = synth.joint_256(n=32)
