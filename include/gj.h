@@ -84,7 +84,10 @@ typedef struct {
     int64_t workspace_bytes; /* device bytes of the per-op workspace */
     int fast_path;           /* 1: the specialised warp-FFT kernels serve this op (FP32,
                                 Nx = 512 and Ny = 512 or 256, at most Nx/2 prisms and
-                                stations along x and Ny/2 along y) */
+                                stations along x and Ny/2 along y); 2: warp-FFT column
+                                kernels behind the general row kernels (FP32, Ny = 1024,
+                                at most 512 prisms and stations along y, any Nx); 0: the
+                                general kernels */
     int P_row, C_col, L_grp; /* launch shapes of the general kernels (gj_op_tune) */
     int radix_order;         /* radix plan of the general kernels' transforms (gj_op_tune) */
     int recompute;           /* 1: spectra rebuilt per layer (GJ_SETUP_RECOMPUTE_SPECTRA) */
@@ -103,7 +106,9 @@ typedef struct {
  * >= s + n - 1 with prime factors <= 17 (any such size gives the same
  * product).  In FP32, Npad = (512, 512) with at most 256 prisms and stations
  * per direction, or (256, 512) with at most 128 along y, selects the specialised
- * warp-FFT kernels (gj_op_info_t.fast_path); any other size runs the general ones.
+ * warp-FFT kernels; Npad_y = 1024 with at most 512 along y selects warp-FFT column
+ * kernels behind the general row kernels (gj_op_info_t.fast_path); any other size
+ * runs the general kernels.
  * `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
  * Synchronous with respect to the host on return (the op is ready).
  * Returns GJ_ERR_ARG for invalid sizes, GJ_ERR_UNSUPPORTED for a padded size
