@@ -419,6 +419,183 @@ __global__ void __launch_bounds__(CWA * 32, 1) k_col_adj1024(View2<R> V, const i
     if (!ok) f512::drain(bars[warp], t_fail, t0, t1, V.err);
 }
 
+// ---------------------------------------------------------------------------
+// Row passes for N_x = 1024 (with the N_y = 1024 column kernels): real lines <->
+// half spectra in the transposed layout, through the general kernels' per-element
+// functors.  A CTA of RW warps runs one complex transform per warp: two lines of one
+// field (pair map, joint = 0) or one line of each field (joint = 1).  The half
+// spectra of the CTA's lines meet in a shared tile [slot][k < 513] (slot stride 513,
+// odd, so that a warp's 16 slots of one k fall in distinct bank pairs) and move to or
+// from the transposed layout with consecutive lines in consecutive words; each thread
+// keeps one slot, so its line's address is formed once.  The warps' transform buffers
+// share the tile's memory (barriers separate the two uses), so that two CTAs fit an SM.
+
+constexpr int RW = 8;                 // warps (transforms) per CTA
+constexpr int RSLOT = 2 * RW;         // tile slots: two lines per transform
+constexpr int NCR = N / 2 + 1;        // 513 bins
+constexpr int TP = NCR;               // tile slot stride
+static_assert((RW * 32) % RSLOT == 0, "a thread keeps one tile slot");
+
+// register of spectrum index lambda + 32 m in the forward transform's lane layout
+__host__ __device__ constexpr int reg_of(int m) { return (m & 1) ? 16 + (m >> 1) : (m >> 1); }
+
+// tile slot s of the CTA -> its line and field, and whether it exists
+__device__ __forceinline__ bool slot_line(const PairMap &pm, int base, int s, int &line, int &field) {
+    const int np = pm.npairs();
+    if (pm.joint) {
+        field = s / RW;
+        const int q = base + (s % RW);
+        line = q;
+        return q < np;
+    }
+    field = 0;
+    const int q = base + (s >> 1);
+    line = 2 * q + (s & 1);
+    return q < np && line < pm.nlines;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tab_plain(cpx<R> *tab, const cpx<R> *src) {
+    for (int i = threadIdx.x; i < Tab1024<R>::WORDS; i += blockDim.x) tab[i] = __ldg(src + i);
+}
+
+// words of the tile / transform-buffer overlay
+constexpr int row_overlay_words() { return RSLOT * TP > RW * N ? RSLOT * TP : RW * N; }
+
+template <typename R, class Pro>
+__global__ void __launch_bounds__(RW * 32, 2) k_row_fwd1024(OpView<R> op, PairMap pm, int n_in, cpx<R> *out0,
+                                                            cpx<R> *out1, const cpx<R> *tab_src, Pro pro,
+                                                            const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tab = reinterpret_cast<C *>(smem_raw);
+    C *tile = tab + Tab1024<R>::WORDS;  // [RSLOT][TP], or the warps' buffers before it is filled
+    __shared__ double red[128];
+    pro.init();
+    load_tab_plain<R>(tab, tab_src);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int base = blockIdx.x * RW, q = base + warp;
+    const bool act = q < pm.npairs();
+    C *buf = tile + warp * N;
+    C v[32];
+    if (act) {
+        int la, lb;
+        bool hb;
+        pm.lines(q, la, lb, hb);
+        // every element through the functor once, then the lane layout of the transform
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = lane + 32 * i;
+            R a = 0, b = 0;
+            if (e < n_in) pro.fetch(la, lb, hb, e, a, b);
+            buf[e] = mk<C>(a, b);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = buf[l + 16 * j];
+        __syncwarp();
+        fwd1024<R>(v, buf, tab);
+    }
+    __syncthreads();  // the buffers become the tile
+    if (act) {
+        // Z = FFT(a + i b) -> A = (Z[k] + conj Z[N - k]) / 2, B = (Z[k] - conj Z[N - k]) / 2i,
+        // k <= 512.  For lambda != 0, Z[N - k] sits in lane (h, 16 - l - h) at m' = 31 - m;
+        // lane 0 (lambda = 0) holds it at m' = 32 - m.
+        const int sa = pm.joint ? warp : 2 * warp, sb = pm.joint ? RW + warp : 2 * warp + 1;
+        const int partner = h ? 31 - l : ((16 - l) & 15);
+        const int lam = 2 * l + h;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            C zm;
+            zm.x = __shfl_sync(0xffffffffu, v[reg_of(31 - m)].x, partner);
+            zm.y = __shfl_sync(0xffffffffu, v[reg_of(31 - m)].y, partner);
+            if (lane == 0) zm = v[reg_of((32 - m) & 31)];
+            const C zk = v[reg_of(m)];
+            const int k = lam + 32 * m;
+            tile[sa * TP + k] = mk<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+            tile[sb * TP + k] = mk<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        }
+        if (lane == 0) {  // k = 512 is its own partner
+            tile[sa * TP + H] = mk<C>(v[reg_of(16)].x, R(0));
+            tile[sb * TP + H] = mk<C>(v[reg_of(16)].y, R(0));
+        }
+    }
+    __syncthreads();
+    {
+        const int s = threadIdx.x % RSLOT;
+        int line, field;
+        if (slot_line(pm, base, s, line, field)) {
+            C *o = (field ? out1 : out0) + pm.at(line, 0, op.ncol, op.tcol);
+            const size_t step = op.tcol ? (size_t)op.tcol : 1;
+            for (int k = threadIdx.x / RSLOT; k < NCR; k += blockDim.x / RSLOT) o[k * step] = tile[s * TP + k];
+        }
+    }
+    pro.flush(red);
+}
+
+template <typename R, class Epi>
+__global__ void __launch_bounds__(RW * 32, 2) k_row_inv1024(OpView<R> op, PairMap pm, int n_out, const cpx<R> *in0,
+                                                            const cpx<R> *in1, const cpx<R> *tab_src, Epi epi,
+                                                            const int *done) {
+    using C = cpx<R>;
+    if (stopped(done)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tab = reinterpret_cast<C *>(smem_raw);
+    C *tile = tab + Tab1024<R>::WORDS;  // [RSLOT][TP], then the warps' buffers
+    __shared__ double red[128];
+    epi.init();
+    load_tab_plain<R>(tab, tab_src);
+    const int base = blockIdx.x * RW;
+    {
+        const int s = threadIdx.x % RSLOT;
+        int line, field;
+        const bool ok = slot_line(pm, base, s, line, field);
+        const C *src = ok ? (field ? in1 : in0) + pm.at(line, 0, op.ncol, op.tcol) : nullptr;
+        const size_t step = op.tcol ? (size_t)op.tcol : 1;
+        for (int k = threadIdx.x / RSLOT; k < NCR; k += blockDim.x / RSLOT)
+            tile[s * TP + k] = ok ? src[k * step] : czero<C>();
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
+    const int q = base + warp;
+    const bool act = q < pm.npairs();
+    int la = 0, lb = 0;
+    bool hb = false;
+    C v[32];
+    if (act) {
+        pm.lines(q, la, lb, hb);
+        const int sa = pm.joint ? warp : 2 * warp, sb = pm.joint ? RW + warp : 2 * warp + 1;
+        const int lam = 2 * l + h;
+        // Hermitian-extended A + i B in the lane layout (an absent second line reads as zero)
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            const int k = lam + 32 * m;
+            const bool lo = k <= H;
+            const int kk = lo ? k : N - k;
+            C A = tile[sa * TP + kk], B = tile[sb * TP + kk];
+            if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
+            v[reg_of(m)] = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+        }
+    }
+    __syncthreads();  // the tile becomes the warps' buffers
+    if (act) {
+        C out[16];
+        inv1024<R>(v, tile + warp * N, tab, out);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int n = l + 16 * (16 * h + jj);
+            if (n < n_out) epi.store(la, lb, hb, n, out[jj].x, out[jj].y);
+        }
+    }
+    epi.flush(red);
+}
+
+template <typename R> inline size_t smem_row() {
+    return ((size_t)Tab1024<R>::WORDS + (size_t)row_overlay_words()) * sizeof(cpx<R>);
+}
+
 template <typename R> inline size_t smem_col_fwd() {
     return (size_t)CWF * ((size_t)ST * (H + N) + N) * sizeof(cpx<R>) + Tab1024<R>::WORDS * sizeof(cpx<R>);
 }

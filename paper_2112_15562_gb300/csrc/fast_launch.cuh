@@ -132,5 +132,27 @@ inline void col_adj(const f512::View2<R> &V, int grid, const int *done, cudaStre
     k_col_adj1024<R><<<grid, CWA * 32, smem_col_adj<R>(), st>>>(V, done);
 }
 
+// the N_x = 1024 row passes (the operator's Tab1024 serves the rows too when N_x = N_y)
+template <typename R, class Pro>
+inline void set_row_fwd_attr() { allow_max_smem(k_row_fwd1024<R, Pro>); }
+template <typename R, class Epi>
+inline void set_row_inv_attr() { allow_max_smem(k_row_inv1024<R, Epi>); }
+inline int row_grid(const PairMap &pm) {
+    const int np = pm.joint ? pm.nlines : (pm.nlines + 1) / 2;
+    return (np + RW - 1) / RW;
+}
+template <typename R, class Pro>
+inline void row_fwd(const OpView<R> &v, const PairMap &pm, int n_in, cpx<R> *o0, cpx<R> *o1, const void *tab,
+                    const Pro &pro, const int *done, cudaStream_t st) {
+    k_row_fwd1024<R, Pro><<<row_grid(pm), RW * 32, smem_row<R>(), st>>>(v, pm, n_in, o0, o1,
+                                                                        static_cast<const cpx<R> *>(tab), pro, done);
+}
+template <typename R, class Epi>
+inline void row_inv(const OpView<R> &v, const PairMap &pm, int n_out, const cpx<R> *i0, const cpx<R> *i1,
+                    const void *tab, const Epi &epi, const int *done, cudaStream_t st) {
+    k_row_inv1024<R, Epi><<<row_grid(pm), RW * 32, smem_row<R>(), st>>>(v, pm, n_out, i0, i1,
+                                                                        static_cast<const cpx<R> *>(tab), epi, done);
+}
+
 }  // namespace f1024
 }  // namespace gj

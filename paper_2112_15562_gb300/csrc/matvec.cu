@@ -59,6 +59,11 @@ static void fast1024_forward(const gj_op *a, const gj_op *b, const float *m0, co
     allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
     allow_max_smem(k_row_inv<R, StorePlain<R>>);
     f1024::set_col_attr<R>();
+    const bool rows1024 = a->Nx == 1024;  // warp-FFT rows as well
+    if (rows1024) {
+        f1024::set_row_fwd_attr<R, LoadPlain<R>>();
+        f1024::set_row_inv_attr<R, StorePlain<R>>();
+    }
     const gj_op *ops[2] = {a, b};
     const float *ms[2] = {m0, m1};
     float *ds[2] = {d0, d1};
@@ -68,8 +73,11 @@ static void fast1024_forward(const gj_op *a, const gj_op *b, const float *m0, co
         OpView<R> v = view_of<R>(o);
         PairMap pm{o->nz * o->ny, 0, o->ny};
         const int npr = (pm.nlines + 1) / 2;
-        k_row_fwd<R, LoadPlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
-                                                                        LoadPlain<R>{ms[i], ms[i], o->nx}, nullptr);
+        const LoadPlain<R> lp{ms[i], ms[i], o->nx};
+        if (rows1024)
+            f1024::row_fwd<R>(v, pm, o->nx, v.Z, v.Z, o->twtab, lp, nullptr, st);
+        else
+            k_row_fwd<R, LoadPlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z, lp, nullptr);
     }
     f1024::col_fwd<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
     for (int i = 0; i < nf; ++i) {
@@ -77,8 +85,11 @@ static void fast1024_forward(const gj_op *a, const gj_op *b, const float *m0, co
         OpView<R> v = view_of<R>(o);
         PairMap ps{o->sy, 0, o->sy};
         const int nps = (ps.nlines + 1) / 2;
-        k_row_inv<R, StorePlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W,
-                                                                         StorePlain<R>{ds[i], ds[i], o->sx}, nullptr);
+        const StorePlain<R> sp{ds[i], ds[i], o->sx};
+        if (rows1024)
+            f1024::row_inv<R>(v, ps, o->sx, v.W, v.W, o->twtab, sp, nullptr, st);
+        else
+            k_row_inv<R, StorePlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.W, v.W, sp, nullptr);
     }
 }
 
@@ -91,6 +102,11 @@ static void fast1024_adjoint(const gj_op *a, const gj_op *b, const float *r0, co
     allow_max_smem(k_row_fwd<R, LoadPlain<R>>);
     allow_max_smem(k_row_inv<R, StorePlain<R>>);
     f1024::set_col_attr<R>();
+    const bool rows1024 = a->Nx == 1024;
+    if (rows1024) {
+        f1024::set_row_fwd_attr<R, LoadPlain<R>>();
+        f1024::set_row_inv_attr<R, StorePlain<R>>();
+    }
     const gj_op *ops[2] = {a, b};
     const float *rs[2] = {r0, r1};
     float *gs[2] = {g0, g1};
@@ -100,8 +116,11 @@ static void fast1024_adjoint(const gj_op *a, const gj_op *b, const float *r0, co
         OpView<R> v = view_of<R>(o);
         PairMap ps{o->sy, 0, o->sy};
         const int nps = (ps.nlines + 1) / 2;
-        k_row_fwd<R, LoadPlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.V, v.V,
-                                                                        LoadPlain<R>{rs[i], rs[i], o->sx}, nullptr);
+        const LoadPlain<R> lp{rs[i], rs[i], o->sx};
+        if (rows1024)
+            f1024::row_fwd<R>(v, ps, o->sx, v.V, v.V, o->twtab, lp, nullptr, st);
+        else
+            k_row_fwd<R, LoadPlain<R>><<<(nps + P - 1) / P, 256, rsm, st>>>(v, ps, o->sx, P, v.V, v.V, lp, nullptr);
     }
     f1024::col_adj<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
     for (int i = 0; i < nf; ++i) {
@@ -109,8 +128,11 @@ static void fast1024_adjoint(const gj_op *a, const gj_op *b, const float *r0, co
         OpView<R> v = view_of<R>(o);
         PairMap pm{o->nz * o->ny, 0, o->ny};
         const int npr = (pm.nlines + 1) / 2;
-        k_row_inv<R, StorePlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z,
-                                                                         StorePlain<R>{gs[i], gs[i], o->nx}, nullptr);
+        const StorePlain<R> sp{gs[i], gs[i], o->nx};
+        if (rows1024)
+            f1024::row_inv<R>(v, pm, o->nx, v.Z, v.Z, o->twtab, sp, nullptr, st);
+        else
+            k_row_inv<R, StorePlain<R>><<<(npr + P - 1) / P, 256, rsm, st>>>(v, pm, o->nx, P, v.Z, v.Z, sp, nullptr);
     }
 }
 

@@ -695,6 +695,7 @@ struct SolverLaunch {
     f512::View2<R> V2;
     bool fast = false;
     bool fast1024 = false;  // general row kernels (transposed intermediates) + N_y = 1024 column kernels
+    bool rows1024 = false;  // fast1024 with N_x = 1024: the warp-FFT row kernels of fast1024.cuh
     FieldVecs<R> F;
     int P, C, L;
     int grid;  // CTAs of the persistent fast-path launches
@@ -709,6 +710,7 @@ struct SolverLaunch {
         if constexpr (std::is_same_v<R, float>) {
             fast = o->fast && sv->op[1]->fast;
             fast1024 = o->fast1024 && sv->op[1]->fast1024;
+            rows1024 = fast1024 && o->Nx == 1024;
             if (fast || fast1024) V2 = f512::make_view2<R>(sv->op[0], sv->op[1]);
         }
         const size_t cs = sizeof(cpx<R>);
@@ -760,7 +762,15 @@ struct SolverLaunch {
             set_col_attr<R>();
             return;
         }
-        if constexpr (std::is_same_v<R, float>) if (fast1024) f1024::set_col_attr<R>();
+        if constexpr (std::is_same_v<R, float>) if (fast1024) {
+            f1024::set_col_attr<R>();
+            f1024::set_row_fwd_attr<R, ProModel<R>>();
+            f1024::set_row_fwd_attr<R, ProDirection<R>>();
+            f1024::set_row_fwd_attr<R, LoadPair<R>>();
+            f1024::set_row_inv_attr<R, EpiResidual<R>>();
+            f1024::set_row_inv_attr<R, EpiGradient<R>>();
+            f1024::set_row_inv_attr<R, EpiQNorm<R>>();
+        }
         allow_max_smem(k_row_fwd<R, ProModel<R>>);
         allow_max_smem(k_row_fwd<R, ProDirection<R>>);
         allow_max_smem(k_row_fwd<R, LoadPair<R>>);
@@ -771,6 +781,27 @@ struct SolverLaunch {
         allow_max_smem(k_col_inv<R>);
         allow_max_smem(k_col_fft<R>);
         allow_max_smem(k_col_adj<R>);
+    }
+
+    // Row passes of the general path over both fields (joint pair maps): the block FFT
+    // kernels, or at N_x = 1024 with the N_y = 1024 columns the warp-FFT row kernels.
+    template <class Pro>
+    void rows_fwd(const PairMap &pm, int n_in, cpx<R> *o0, cpx<R> *o1, const Pro &pro, const int *done,
+                  cudaStream_t st) {
+        if constexpr (std::is_same_v<R, float>) if (rows1024) {
+            f1024::row_fwd<R>(v0, pm, n_in, o0, o1, sv->op[0]->twtab, pro, done, st);
+            return;
+        }
+        k_row_fwd<R, Pro><<<(pm.nlines + P - 1) / P, 256, rsm, st>>>(v0, pm, n_in, P, o0, o1, pro, done);
+    }
+    template <class Epi>
+    void rows_inv(const PairMap &pm, int n_out, const cpx<R> *i0, const cpx<R> *i1, const Epi &epi, const int *done,
+                  cudaStream_t st) {
+        if constexpr (std::is_same_v<R, float>) if (rows1024) {
+            f1024::row_inv<R>(v0, pm, n_out, i0, i1, sv->op[0]->twtab, epi, done, st);
+            return;
+        }
+        k_row_inv<R, Epi><<<(pm.nlines + P - 1) / P, 256, rsm, st>>>(v0, pm, n_out, P, i0, i1, epi, done);
     }
 
     // Forward columns (Y = sum_r T^_r FFT_y(Z_r)) and inverse columns, both fields.
@@ -844,11 +875,11 @@ struct SolverLaunch {
         }
         PairMap pc{o->nz * o->ny, 1, o->ny};
         ProModel<R> pm{F, sv->S, o->nx, o->ny};
-        k_row_fwd<R, ProModel<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pm, done);
+        rows_fwd(pc, o->nx, v0.Z, v1.Z, pm, done, st);
         forward_columns(st);
         PairMap ps{o->sy, 1, o->sy};
         EpiResidual<R> er{F, sv->S, o->sx};
-        k_row_inv<R, EpiResidual<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, er, done);
+        rows_inv(ps, o->sx, v0.W, v1.W, er, done, st);
         k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
     }
 
@@ -885,8 +916,7 @@ struct SolverLaunch {
         bool cols1024 = false;
         if constexpr (std::is_same_v<R, float>) cols1024 = fast1024;
         if (cols1024) {
-            k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.V, v1.V, lv,
-                                                                                done);
+            rows_fwd(ps, o->sx, v0.V, v1.V, lv, done, st);
             if constexpr (std::is_same_v<R, float>) f1024::col_adj<R>(V2, grid, done, st);
         } else {
             k_row_fwd<R, LoadPair<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, lv,
@@ -895,13 +925,13 @@ struct SolverLaunch {
             k_col_adj<R><<<dim3(nt, o->nz, 2), 256, csm, st>>>(v0, v1, C, done);
         }
         EpiGradient<R> eg{F, sv->S, o->nx, o->ny};
-        k_row_inv<R, EpiGradient<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, eg, done);
+        rows_inv(pc, o->nx, v0.Z, v1.Z, eg, done, st);
         // direction and its forward product
         ProDirection<R> pd{F, sv->S, o->nx, o->ny};
-        k_row_fwd<R, ProDirection<R>><<<(pc.nlines + P - 1) / P, 256, rsm, st>>>(v0, pc, o->nx, P, v0.Z, v1.Z, pd, done);
+        rows_fwd(pc, o->nx, v0.Z, v1.Z, pd, done, st);
         forward_columns(st);
         EpiQNorm<R> eq{F, sv->S, o->sx};
-        k_row_inv<R, EpiQNorm<R>><<<(ps.nlines + P - 1) / P, 256, rsm, st>>>(v0, ps, o->sx, P, v0.W, v1.W, eq, done);
+        rows_inv(ps, o->sx, v0.W, v1.W, eq, done, st);
         k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
         // model update, its forward product and the chi^2 scalars
         head(st);

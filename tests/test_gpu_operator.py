@@ -47,6 +47,9 @@ CASES = {
     "cols1024_ragged": (_grid(13, 11, 20, 9, 2, dx=40.0, dy=55.0, off=(3, 0)), (1024, 36)),
     "cols1024_odd_lines": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (1024, 15)),
     "cols1024_wide": (_grid(30, 6, 24, 6, 2, dx=20.0), (1024, 1024)),
+    # N_x = 1024 as well: the warp-FFT row kernels of the same file
+    "rows1024_ragged": (_grid(13, 11, 20, 9, 3, dx=40.0, dy=55.0, off=(3, 0)), (1024, 1024)),
+    "rows1024_odd": (_grid(7, 5, 7, 5, 5, station_z=-8.0, zvar=True), (1024, 1024)),
 }
 
 FAST = {(512, 512), (256, 512)}
@@ -197,7 +200,7 @@ def test_joint_256_sampled_rows(gj, c3_tables, prec):
 
 
 @pytest.mark.parametrize("case", ["fast512_small", "fast512_ragged", "joint16", "fast256_ragged", "fast256_odd_lines",
-                                  "cols1024_ragged", "cols1024_odd_lines"])
+                                  "cols1024_ragged", "cols1024_odd_lines", "cols1024_wide"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_pair_products_match_dense_oracle(gj, case, prec):
     """gj_g_forward_pair / gj_g_adjoint_pair: both fields in one call (one set of joint

@@ -141,7 +141,7 @@ def test_stepwise_graph_and_eager_match_one_shot(small, graph):
         assert rel(m2[i], m1[i]) <= 1e-12
 
 
-@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 32)])
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 32), (1024, 1024)])
 def test_joint_fp32_on_the_512_kernels(small, npad):
     """The same solve with 512 x 512 (or 256 x 512) embeddings, served by the
     specialised kernels."""
@@ -199,7 +199,7 @@ def ragged():
     return (w,) + joint_case(w)
 
 
-@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 30)])
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 30), (1024, 1024)])
 @pytest.mark.parametrize("optional", [False, True])
 def test_fast_solver_partial_line_groups(ragged, optional, npad):
     """13 rows per layer: the 512 kernels' cell-line passes, which take aligned groups

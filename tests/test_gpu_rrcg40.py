@@ -56,7 +56,7 @@ def check(name, ref, m, rep, kmax):
         assert m[i].min() >= np.float32(KW["lo"][i]) and m[i].max() <= np.float32(KW["hi"][i])
 
 
-@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 64)])
+@pytest.mark.parametrize("npad", [(512, 512), (256, 512), (1024, 64), (1024, 1024)])
 def test_fast_joint_solve_40_layers_against_dense_oracle(npad):
     gj = lib()
     w = synth.joint_256(n=32)
