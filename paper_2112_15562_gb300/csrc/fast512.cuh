@@ -266,6 +266,22 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "l"(src), "r"(bytes), "r"(s_addr(bar))
         : "memory");
 }
+// The same copy with an L2 policy (createpolicy): the column passes read each layer
+// spectrum once per product, so its lines go first when L2 needs room and the
+// row passes' intermediates stay longer.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void bulk_load_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                               uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            s_addr(dst)),
+        "l"(src), "r"(bytes), "r"(s_addr(bar)), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -416,6 +432,7 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
     cu.set(t0, nz, V.nfield);
     ci = cu;
     int ti = t0;
+    const uint64_t pol = l2_evict_first();
     auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
         const int s = (ti - t0) % CSTAGES;
         const OpView<R> &op = V.op[ci.fld];
@@ -423,11 +440,11 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_fwd512(View2<R> V, const
         if (op.real_spec) {
             mbar_expect(&bars[warp][s], ZB + KEB);
             bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(op.spec) + off * KE, KEB, &bars[warp][s]);
+            bulk_load_hint(ts + s * N, reinterpret_cast<const R *>(op.spec) + off * KE, KEB, &bars[warp][s], pol);
         } else {
             mbar_expect(&bars[warp][s], ZB + TB);
             bulk_load(zs + s * H, op.Z + off * H, ZB, &bars[warp][s]);
-            bulk_load(ts + s * N, op.spec + off * N, TB, &bars[warp][s]);
+            bulk_load_hint(ts + s * N, op.spec + off * N, TB, &bars[warp][s], pol);
         }
         ++ti;
         ci.next(nz, V.nfield);
@@ -559,15 +576,17 @@ __global__ void __launch_bounds__(CWARPS * 32, 1) k_col_adj512(View2<R> V, const
     cu.set(t0, nz, V.nfield);
     ci = cu;
     int ti = t0;
+    const uint64_t pol = l2_evict_first();
     auto issue = [&]() {  // item ti into stage (ti - t0) % CSTAGES
         const int s = (ti - t0) % CSTAGES;
         const size_t off = (size_t)ci.r * NC + ci.kx;
         if (V.op[ci.fld].real_spec) {
             mbar_expect(&bars[warp][s], KEB);
-            bulk_load(ts + s * N, reinterpret_cast<const R *>(V.op[ci.fld].spec) + off * KE, KEB, &bars[warp][s]);
+            bulk_load_hint(ts + s * N, reinterpret_cast<const R *>(V.op[ci.fld].spec) + off * KE, KEB, &bars[warp][s],
+                           pol);
         } else {
             mbar_expect(&bars[warp][s], TB);
-            bulk_load(ts + s * N, V.op[ci.fld].spec + off * N, TB, &bars[warp][s]);
+            bulk_load_hint(ts + s * N, V.op[ci.fld].spec + off * N, TB, &bars[warp][s], pol);
         }
         ++ti;
         ci.next(nz, V.nfield);
