@@ -1222,6 +1222,22 @@ extern "C" void gj_rrcg_destroy(gj_rrcg *sv) {
     delete sv;
 }
 
+// Two page-locked ints per host thread for the one-shot solve's stop flags,
+// allocated on first use and kept for the life of the process (portable: any
+// device may write them).  NULL if page-locked memory is not available.
+static int *pinned_flags() {
+    thread_local int *p = nullptr;
+    thread_local bool tried = false;
+    if (!tried) {
+        tried = true;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&p), 2 * sizeof(int), cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    return p;
+}
+
 extern "C" gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrcg_params *P,
                                          const void *const dobs[2], const void *const sigma[2],
                                          const void *const m_apr[2], const void *const w_depth[2],
@@ -1231,17 +1247,37 @@ extern "C" gj_status gj_rrcg_joint_solve(const gj_op *const ops[2], const gj_rrc
     gj_rrcg *sv = nullptr;
     gj_status rc = gj_rrcg_create(ops, P, dobs, sigma, m_apr, w_depth, w_hard, m, hist, stream, &sv);
     if (rc != GJ_OK) return rc;
+    // Iterations go in chunks of eight graph replays.  The stop flag of chunk c - 1 is
+    // copied into page-locked memory behind it and read while chunk c runs, so the
+    // device never waits for the host; a chunk queued after the stop does no work
+    // (every kernel returns at the flag).
     int left = P->kmax;
     const int chunk = 8;
-    while (left > 0) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int *flags = pinned_flags();
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (flags && (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess))
+        flags = nullptr;
+    for (int c = 0; left > 0; ++c) {
         const int it = std::min(chunk, left);
         rc = gj_rrcg_iterate(sv, it, 1, stream);
         if (rc != GJ_OK) break;
         left -= it;
-        const int d = gj_rrcg_done(sv, stream);
-        if (d < 0) { rc = cuda_fail(cudaGetLastError(), "gj_rrcg_joint_solve"); break; }
-        if (d) break;
+        if (!flags) {  // no page-locked flag: a synchronous check after each chunk
+            const int d = gj_rrcg_done(sv, stream);
+            if (d < 0) { rc = cuda_fail(cudaGetLastError(), "gj_rrcg_joint_solve"); break; }
+            if (d) break;
+            continue;
+        }
+        cudaError_t e = cudaMemcpyAsync(flags + (c & 1), &sv->S->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[c & 1], st);
+        if (e == cudaSuccess && c > 0) e = cudaEventSynchronize(ev[(c - 1) & 1]);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "gj_rrcg_joint_solve: stop flag"); break; }
+        if (c > 0 && flags[(c - 1) & 1]) break;
     }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (rc == GJ_OK) rc = gj_rrcg_report_get(sv, rep, stream);
     gj_rrcg_destroy(sv);
     if (rc == GJ_OK && rep->status != GJ_OK) {
