@@ -647,6 +647,8 @@ def c5_leg(gj, torch, dev, flush, hbm):
         ts = []
         for k in range(steps + 1):
             flush.fill_(float(k))
+            for t in m:
+                t.grad = None  # as an optimiser's zero_grad(set_to_none=True): no accumulation kernel
             e0.record()
             for i in range(2):
                 gj.G(ops[i], m[i]).backward(gd[i])

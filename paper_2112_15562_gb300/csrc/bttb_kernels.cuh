@@ -62,6 +62,32 @@ __device__ __forceinline__ bool stopped(const int *done) {
     return done != nullptr && *(volatile const int *)done != 0;
 }
 
+// Block-strided loop over it < total in batches of U elements per thread: the U
+// loads of a batch are issued before any of its stores, so that a thread keeps U
+// global reads in flight instead of one.
+template <int U, class Load, class Store>
+__device__ __forceinline__ void staged_loop(int total, Load load, Store store) {
+    for (int it0 = threadIdx.x; it0 < total; it0 += U * blockDim.x) {
+        decltype(load(0)) v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = it0 + u * (int)blockDim.x;
+            if (it < total) v[u] = load(it);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = it0 + u * (int)blockDim.x;
+            if (it < total) store(it, v[u]);
+        }
+    }
+}
+constexpr int kStageU = 8;  // loads in flight per thread in the general kernels' staging loops
+// Batch of a row functor's staging loop: Pro::STAGE_U where the functor states it
+// (a functor whose fetch is long arithmetic keeps 1, so that its code is not
+// replicated), else 4.
+template <class F, class = void> struct StageU { static constexpr int value = 4; };
+template <class F> struct StageU<F, decltype((void)F::STAGE_U)> { static constexpr int value = F::STAGE_U; };
+
 // ---------------------------------------------------------------------------
 // Row pass, real -> half spectrum.  Pro::fetch(la, lb, hasb, j, a, b) supplies the
 // two real inputs of element j (< n_in); Pro::flush(scratch) runs once per block.
@@ -80,16 +106,19 @@ __global__ void __launch_bounds__(256) k_row_fwd(OpView<R> op, PairMap pm, int n
     pro.init();
     const int q0 = blockIdx.x * P;
     const int np = pm.npairs();
-    for (int it = threadIdx.x; it < n_in * P; it += blockDim.x) {
-        const int p = it % P, j = it / P, q = q0 + p;
-        R a = 0, b = 0;
-        if (q < np) {
-            int la, lb; bool hb;
-            pm.lines(q, la, lb, hb);
-            pro.fetch(la, lb, hb, j, a, b);
-        }
-        buf0[j * P + p] = mk<C>(a, b);
-    }
+    staged_loop<StageU<Pro>::value>(
+        n_in * P,
+        [&](int it) {
+            const int p = it % P, j = it / P, q = q0 + p;
+            R a = 0, b = 0;
+            if (q < np) {
+                int la, lb; bool hb;
+                pm.lines(q, la, lb, hb);
+                pro.fetch(la, lb, hb, j, a, b);
+            }
+            return mk<C>(a, b);
+        },
+        [&](int it, C z) { buf0[it] = z; });
     __syncthreads();
     C *X = fft_lines<R, false>(buf0, buf1, op.px, P, tw, n_in);
     for (int it = threadIdx.x; it < ncol * P; it += blockDim.x) {
@@ -123,21 +152,24 @@ __global__ void __launch_bounds__(256) k_row_inv(OpView<R> op, PairMap pm, int n
     epi.init();
     const int q0 = blockIdx.x * P;
     const int np = pm.npairs();
-    for (int it = threadIdx.x; it < N * P; it += blockDim.x) {
-        const int p = it % P, k = it / P, q = q0 + p;
-        C z = czero<C>();
-        if (q < np) {
-            int la, lb; bool hb;
-            pm.lines(q, la, lb, hb);
-            const bool lo = k < ncol;
-            const int kk = lo ? k : N - k;
-            C A = in0[pm.at(la, kk, ncol, op.tcol)];
-            C B = hb ? in1[pm.at(lb, kk, ncol, op.tcol)] : czero<C>();
-            if (kk == 0 || 2 * kk == N) { A.y = 0; B.y = 0; }
-            z = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
-        }
-        buf0[k * P + p] = z;
-    }
+    staged_loop<kStageU>(
+        N * P,
+        [&](int it) {
+            const int p = it % P, k = it / P, q = q0 + p;
+            C z = czero<C>();
+            if (q < np) {
+                int la, lb; bool hb;
+                pm.lines(q, la, lb, hb);
+                const bool lo = k < ncol;
+                const int kk = lo ? k : N - k;
+                C A = in0[pm.at(la, kk, ncol, op.tcol)];
+                C B = hb ? in1[pm.at(lb, kk, ncol, op.tcol)] : czero<C>();
+                if (kk == 0 || 2 * kk == N) { A.y = 0; B.y = 0; }
+                z = lo ? mk<C>(A.x - B.y, A.y + B.x) : mk<C>(A.x + B.y, B.x - A.y);
+            }
+            return z;
+        },
+        [&](int it, C z) { buf0[it] = z; });
     __syncthreads();
     C *X = fft_lines<R, true>(buf0, buf1, op.px, P, tw, N);
     for (int it = threadIdx.x; it < n_out * P; it += blockDim.x) {
@@ -174,17 +206,25 @@ __global__ void __launch_bounds__(256) k_col_fwd_mac(OpView<R> op0, OpView<R> op
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) acc[it] = czero<Cx>();
     for (int r = r0; r < r1; ++r) {
         const Cx *Zr = op.Z + (size_t)r * ny * ncol;
-        for (int it = threadIdx.x; it < ny * C; it += blockDim.x) {
-            const int c = it % C, iy = it / C;
-            buf0[it] = (c0 + c < ncol) ? Zr[(size_t)iy * ncol + c0 + c] : czero<Cx>();
-        }
+        staged_loop<kStageU>(
+            ny * C,
+            [&](int it) {
+                const int c = it % C, iy = it / C;
+                return (c0 + c < ncol) ? Zr[(size_t)iy * ncol + c0 + c] : czero<Cx>();
+            },
+            [&](int it, Cx z) { buf0[it] = z; });
         __syncthreads();
         const Cx *X = fft_lines<R, false>(buf0, buf1, op.py, C, tw, ny);
         const Cx *Tr = op.spec + (size_t)(r - op.spec_r0) * Ny * ncol;
-        for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
-            const int c = it % C, ky = it / C;
-            if (c0 + c < ncol) acc[it] = cadd(acc[it], cmul(X[it], Tr[(size_t)ky * ncol + c0 + c]));
-        }
+        staged_loop<kStageU>(
+            Ny * C,
+            [&](int it) {
+                const int c = it % C, ky = it / C;
+                return (c0 + c < ncol) ? Tr[(size_t)ky * ncol + c0 + c] : czero<Cx>();
+            },
+            [&](int it, Cx t) {
+                if (c0 + it % C < ncol) acc[it] = cadd(acc[it], cmul(X[it], t));
+            });
         __syncthreads();
     }
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
@@ -211,10 +251,13 @@ __global__ void __launch_bounds__(256) k_col_inv(OpView<R> op0, OpView<R> op1, i
     Cx *buf1 = buf0 + Ny * C;
     Cx *tw = buf1 + Ny * C;
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
-    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
-        const int c = it % C, ky = it / C;
-        buf0[it] = (c0 + c < ncol) ? op.Y[(size_t)ky * ncol + c0 + c] : czero<Cx>();
-    }
+    staged_loop<kStageU>(
+        Ny * C,
+        [&](int it) {
+            const int c = it % C, ky = it / C;
+            return (c0 + c < ncol) ? op.Y[(size_t)ky * ncol + c0 + c] : czero<Cx>();
+        },
+        [&](int it, Cx z) { buf0[it] = z; });
     __syncthreads();
     const Cx *X = fft_lines<R, true>(buf0, buf1, op.py, C, tw, Ny);
     for (int it = threadIdx.x; it < op.sy * C; it += blockDim.x) {
@@ -238,10 +281,13 @@ __global__ void __launch_bounds__(256) k_col_fft(OpView<R> op0, OpView<R> op1, i
     Cx *buf1 = buf0 + Ny * C;
     Cx *tw = buf1 + Ny * C;
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
-    for (int it = threadIdx.x; it < op.sy * C; it += blockDim.x) {
-        const int c = it % C, iy = it / C;
-        buf0[it] = (c0 + c < ncol) ? op.W[(size_t)iy * ncol + c0 + c] : czero<Cx>();
-    }
+    staged_loop<kStageU>(
+        op.sy * C,
+        [&](int it) {
+            const int c = it % C, iy = it / C;
+            return (c0 + c < ncol) ? op.W[(size_t)iy * ncol + c0 + c] : czero<Cx>();
+        },
+        [&](int it, Cx z) { buf0[it] = z; });
     __syncthreads();
     const Cx *X = fft_lines<R, false>(buf0, buf1, op.py, C, tw, op.sy);
     for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
@@ -267,11 +313,14 @@ __global__ void __launch_bounds__(256) k_col_adj(OpView<R> op0, OpView<R> op1, i
     Cx *tw = buf1 + Ny * C;
     for (int i = threadIdx.x; i < Ny; i += blockDim.x) tw[i] = op.twy[i];
     const Cx *Tr = op.spec + (size_t)(r - op.spec_r0) * Ny * ncol;
-    for (int it = threadIdx.x; it < Ny * C; it += blockDim.x) {
-        const int c = it % C, ky = it / C;
-        buf0[it] = (c0 + c < ncol) ? cmulc(op.Y[(size_t)ky * ncol + c0 + c], Tr[(size_t)ky * ncol + c0 + c])
+    staged_loop<kStageU>(
+        Ny * C,
+        [&](int it) {
+            const int c = it % C, ky = it / C;
+            return (c0 + c < ncol) ? cmulc(op.Y[(size_t)ky * ncol + c0 + c], Tr[(size_t)ky * ncol + c0 + c])
                                    : czero<Cx>();
-    }
+        },
+        [&](int it, Cx z) { buf0[it] = z; });
     __syncthreads();
     const Cx *X = fft_lines<R, true>(buf0, buf1, op.py, C, tw, Ny);
     Cx *Zr = op.Z + (size_t)r * ny * ncol;
@@ -293,6 +342,7 @@ struct LoadPlain {  // a = x0[la*pitch + j], b = x1[lb*pitch + j]
     const R *x1;
     int pitch;
     static constexpr int NPRE = 1;  // rows la of x0 and lb of x1, staged by the 512 team passes
+    static constexpr int STAGE_U = 8;
     __device__ const R *pre_src(int, int i) const { return i == 0 ? x0 : x1; }
     __device__ void init() {}
     __device__ __forceinline__ void fetch(int la, int lb, bool hb, int j, R &a, R &b) const {

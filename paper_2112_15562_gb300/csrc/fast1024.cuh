@@ -454,9 +454,15 @@ __device__ __forceinline__ bool slot_line(const PairMap &pm, int base, int s, in
     return q < np && line < pm.nlines;
 }
 
+// The operator's twiddle table into shared memory with 16-byte asynchronous copies,
+// all in flight at once (committed as one group; the caller waits and synchronises).
 template <typename R>
-__device__ __forceinline__ void load_tab_plain(cpx<R> *tab, const cpx<R> *src) {
-    for (int i = threadIdx.x; i < Tab1024<R>::WORDS; i += blockDim.x) tab[i] = __ldg(src + i);
+__device__ __forceinline__ void load_tab_async(cpx<R> *tab, const cpx<R> *src) {
+    constexpr int CH = Tab1024<R>::WORDS * (int)sizeof(cpx<R>) / 16;
+    const char *s = reinterpret_cast<const char *>(src);
+    char *d = reinterpret_cast<char *>(tab);
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) f512::cp_async16(d + 16 * i, s + 16 * i);
+    f512::cp_async_commit();
 }
 
 // words of the tile / transform-buffer overlay
@@ -473,8 +479,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_fwd1024(OpView<R> op, PairMa
     C *tile = tab + Tab1024<R>::WORDS;  // [RSLOT][TP], or the warps' buffers before it is filled
     __shared__ double red[128];
     pro.init();
-    load_tab_plain<R>(tab, tab_src);
-    __syncthreads();
+    load_tab_async<R>(tab, tab_src);  // in flight while the lines are read
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int base = blockIdx.x * RW, q = base + warp;
     const bool act = q < pm.npairs();
@@ -484,20 +489,25 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_fwd1024(OpView<R> op, PairMa
         int la, lb;
         bool hb;
         pm.lines(q, la, lb, hb);
-        // every element through the functor once, then the lane layout of the transform
+        // every element through the functor once (all loads issued before the first
+        // store), then the lane layout of the transform
+        R a[16], b[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int e = lane + 32 * i;
-            R a = 0, b = 0;
-            if (e < n_in) pro.fetch(la, lb, hb, e, a, b);
-            buf[e] = mk<C>(a, b);
+            a[i] = b[i] = R(0);
+            if (e < n_in) pro.fetch(la, lb, hb, e, a[i], b[i]);
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = buf[l + 16 * j];
         __syncwarp();
-        fwd1024<R>(v, buf, tab);
     }
+    f512::cp_async_wait<0>();
+    __syncthreads();  // the table is in
+    if (act) fwd1024<R>(v, buf, tab);
     __syncthreads();  // the buffers become the tile
     if (act) {
         // Z = FFT(a + i b) -> A = (Z[k] + conj Z[N - k]) / 2, B = (Z[k] - conj Z[N - k]) / 2i,
@@ -546,7 +556,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_inv1024(OpView<R> op, PairMa
     C *tile = tab + Tab1024<R>::WORDS;  // [RSLOT][TP], then the warps' buffers
     __shared__ double red[128];
     epi.init();
-    load_tab_plain<R>(tab, tab_src);
+    load_tab_async<R>(tab, tab_src);
     const int base = blockIdx.x * RW;
     {
         const int s = threadIdx.x % RSLOT;
@@ -554,8 +564,15 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_inv1024(OpView<R> op, PairMa
         const bool ok = slot_line(pm, base, s, line, field);
         const C *src = ok ? (field ? in1 : in0) + pm.at(line, 0, op.ncol, op.tcol) : nullptr;
         const size_t step = op.tcol ? (size_t)op.tcol : 1;
-        for (int k = threadIdx.x / RSLOT; k < NCR; k += blockDim.x / RSLOT)
-            tile[s * TP + k] = ok ? src[k * step] : czero<C>();
+        // every copy of the CTA's half spectra in flight at once (asynchronous copies)
+        for (int k = threadIdx.x / RSLOT; k < NCR; k += blockDim.x / RSLOT) {
+            C *dst = tile + s * TP + k;
+            if (!ok) *dst = czero<C>();
+            else if constexpr (sizeof(C) == 8) f512::cp_async8(dst, src + k * step);
+            else f512::cp_async16(dst, src + k * step);
+        }
+        f512::cp_async_commit();
+        f512::cp_async_wait<0>();
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;

@@ -7,22 +7,6 @@
 namespace gj {
 namespace f512 {
 
-// asynchronous global -> shared copies (cp.async), completed per thread by groups
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() {  // at most NPEND of the newest groups still in flight
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Row pass (x direction), real lines -> half spectra in the transposed layout.
 // A CTA of NW warps runs FPW complex transforms per warp (FFTS = NW * FPW per CTA).

@@ -137,6 +137,7 @@ __device__ double far_cubature(double uc_, double hu_, double vc_, double hv_, d
 // [-(n-1), s-1], zero elsewhere; K is the 8-corner sum of the lattice, or the
 // far-field cubature.
 struct LoadTable {
+    static constexpr int STAGE_U = 1;  // the fetch is the corner differences and the far-field cubature
     const double *lat;
     int nbx1, nby1;
     int Nx, Ny, sx, sy, nx, ny, off_x, off_y, a_max, b_max;
