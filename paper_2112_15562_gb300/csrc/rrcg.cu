@@ -549,8 +549,28 @@ struct EpiQNorm {
     __device__ void flush(double *red) { block_accumulate<2>(acc, S->qq, red); }
 };
 
+// The one-thread scalar steps run on a shared-memory copy of the solver state: a
+// warp copies it in with one coalesced read (instead of a chain of dependent global
+// loads), thread 0 takes the step, and the warp copies the state back.
+static_assert(sizeof(SolverDev) % sizeof(unsigned long long) == 0 && alignof(SolverDev) == 8,
+              "the state copies as 8-byte words");
+constexpr int kStateWords = (int)(sizeof(SolverDev) / sizeof(unsigned long long));
+__device__ __forceinline__ void state_copy(void *dst, const void *src) {
+    for (int i = threadIdx.x; i < kStateWords; i += 32)
+        static_cast<unsigned long long *>(dst)[i] = static_cast<const unsigned long long *>(src)[i];
+}
+template <void (*STEP)(SolverDev *)>
+__device__ __forceinline__ void scalar_step_on_copy(SolverDev *S) {
+    __shared__ SolverDev sh;
+    state_copy(&sh, S);
+    __syncwarp();
+    if (threadIdx.x == 0) STEP(&sh);
+    __syncwarp();
+    state_copy(S, &sh);
+}
+
 // chi^2 test, alpha schedule and stop (Eq. chi2, Eq. regpara); one thread.
-__global__ void k_scalars_after_residual(SolverDev *S) {
+__device__ void scalars_after_residual(SolverDev *S) {
     if (S->done) return;
     const int k = S->k;
     for (int i = 0; i < 2; ++i)
@@ -580,7 +600,7 @@ __global__ void k_scalars_after_residual(SolverDev *S) {
 }
 
 // Step length s_k (RRCG:6); one thread.
-__global__ void k_scalars_after_direction(SolverDev *S) {
+__device__ void scalars_after_direction(SolverDev *S) {
     if (S->done) return;
     const int k = S->k;
     double den[2], beta[2];
@@ -616,6 +636,10 @@ __global__ void k_scalars_after_direction(SolverDev *S) {
     S->pending_update = 1;
     S->k = k + 1;
 }
+
+// one warp each (launched as <<<1, 32>>>)
+__global__ void k_scalars_after_residual(SolverDev *S) { scalar_step_on_copy<scalars_after_residual>(S); }
+__global__ void k_scalars_after_direction(SolverDev *S) { scalar_step_on_copy<scalars_after_direction>(S); }
 
 // The report of the solver state into device memory (one thread): the same fields
 // as gj_rrcg_report_get, without a host round trip.
@@ -870,7 +894,7 @@ struct SolverLaunch {
             // residual, Phi and the residual rows' spectra for the adjoint, in one pass
             EpiResidual<R> er{F, sv->S, o->sx};
             row_resid<R, kDataNW>(V2, o->sy, o->sx, er, done, st);
-            k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
+            k_scalars_after_residual<<<1, 32, 0, st>>>(sv->S);
             return;
         }
         PairMap pc{o->nz * o->ny, 1, o->ny};
@@ -880,7 +904,7 @@ struct SolverLaunch {
         PairMap ps{o->sy, 1, o->sy};
         EpiResidual<R> er{F, sv->S, o->sx};
         rows_inv(ps, o->sx, v0.W, v1.W, er, done, st);
-        k_scalars_after_residual<<<1, 1, 0, st>>>(sv->S);
+        k_scalars_after_residual<<<1, 32, 0, st>>>(sv->S);
     }
 
     void body(cudaStream_t st) {
@@ -903,7 +927,7 @@ struct SolverLaunch {
             forward_columns(st);
             EpiQNorm<R> eq{F, sv->S, o->sx};
             row_inv<R, kDataNW, kDataFPW>(V2, 1, o->sy, o->sy, o->sx, 1, eq, done, st);
-            k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
+            k_scalars_after_direction<<<1, 32, 0, st>>>(sv->S);
             head(st);
             return;
         }
@@ -932,7 +956,7 @@ struct SolverLaunch {
         forward_columns(st);
         EpiQNorm<R> eq{F, sv->S, o->sx};
         rows_inv(ps, o->sx, v0.W, v1.W, eq, done, st);
-        k_scalars_after_direction<<<1, 1, 0, st>>>(sv->S);
+        k_scalars_after_direction<<<1, 32, 0, st>>>(sv->S);
         // model update, its forward product and the chi^2 scalars
         head(st);
     }
