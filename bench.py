@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, operator, e2e and CPU legs")
+    ap.add_argument("--leg", choices=["c5", "fp64"], default=None,
+                    help="time one leg alone at fixed padded sizes (no autotuning), for profiling: c5 = "
+                         "512x512x48 forward + backward of both fields at 1024x1024; fp64 = the plain FP64 "
+                         "iteration at 256x256x40, 512x512")
     return ap.parse_args()
 
 
@@ -830,6 +834,48 @@ def e2e_leg(gj, torch, ops, g, dobs, sigma, wdep, iters=50, calls=3):
                     "both models"}
 
 
+def run_leg(args):
+    """One leg alone, at fixed padded sizes, ``--steps`` timed steps after ``--warmup``
+    (the launch lists of ``profiles/`` come from these runs)."""
+    import torch
+
+    import paper_2112_15562_gb300 as gj
+
+    dev = torch.device("cuda:0")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    if args.leg == "fp64":
+        w, g, ops, dobs, sigma, wdep = build_problem(gj, torch, "fp64", dev, npad=(512, 512))
+        sv, m, P = solver_for(gj, torch, ops, g, dobs, sigma, wdep, args.steps + args.warmup + 2, dev)
+        times, _, _ = time_steps(torch, sv, args.steps, args.warmup, flush, profile=False)
+        sv.close()
+        print(json.dumps({"leg": "fp64 joint RRCG 256x256x40, Npad 512x512", "ms_per_iteration": sum(times) / len(times),
+                          "steps": args.steps}))
+        return
+    import synth
+
+    g = synth.uniform_grid(512, 512, 512, 512, 48, 100.0)
+    mag = synth.Mag(50000.0, 60.0, 10.0)
+    ops = [gj.bttb_setup(g, "gravity", precision="fp32", npad=(1024, 1024)),
+           gj.bttb_setup(g, "magnetic", mag, precision="fp32", npad=(1024, 1024))]
+    m = [torch.rand(g.n, device=dev, requires_grad=True) for _ in range(2)]
+    gd = [torch.randn(g.s, device=dev) for _ in range(2)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        for t in m:
+            t.grad = None
+        e0.record()
+        for i in range(2):
+            gj.G(ops[i], m[i]).backward(gd[i])
+        e1.record()
+        e1.synchronize()
+        if k >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+    print(json.dumps({"leg": "512x512x48 fwd+bwd of both fields, Npad 1024x1024, FP32",
+                      "ms_per_fwd_bwd_both_fields": statistics.median(ts), "steps": args.steps}))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -837,6 +883,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.leg:
+        run_leg(args)
         return
     if world > 1:
         import torch

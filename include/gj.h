@@ -85,8 +85,9 @@ typedef struct {
     int fast_path;           /* 1: the specialised warp-FFT kernels serve this op (FP32,
                                 Nx = 512 and Ny = 512 or 256, at most Nx/2 prisms and
                                 stations along x and Ny/2 along y); 2: warp-FFT column
-                                kernels behind the general row kernels (FP32, Ny = 1024,
-                                at most 512 prisms and stations along y, any Nx); 0: the
+                                kernels (FP32, Ny = 1024, at most 512 prisms and stations
+                                along y, any Nx) behind warp-FFT row kernels when
+                                Nx = 1024 and the general row kernels otherwise; 0: the
                                 general kernels */
     int P_row, C_col, L_grp; /* launch shapes of the general kernels (gj_op_tune) */
     int radix_order;         /* radix plan of the general kernels' transforms (gj_op_tune) */
@@ -107,8 +108,9 @@ typedef struct {
  * product).  In FP32, Npad = (512, 512) with at most 256 prisms and stations
  * per direction, or (256, 512) with at most 128 along y, selects the specialised
  * warp-FFT kernels; Npad_y = 1024 with at most 512 along y selects warp-FFT column
- * kernels behind the general row kernels (gj_op_info_t.fast_path); any other size
- * runs the general kernels.
+ * kernels, behind warp-FFT row kernels when Npad_x = 1024 and the general row
+ * kernels otherwise (gj_op_info_t.fast_path); any other size runs the general
+ * kernels.
  * `mag` is required for GJ_MAGNETIC and ignored for GJ_GRAVITY.
  * Synchronous with respect to the host on return (the op is ready).
  * Returns GJ_ERR_ARG for invalid sizes, GJ_ERR_UNSUPPORTED for a padded size
