@@ -283,6 +283,21 @@ def solver_for(gj, torch, ops, g, dobs, sigma, wdep, kmax, dev):
     return gj.Solver(ops, P, dobs, sigma, wdep, m), m, P
 
 
+def queued_times(torch, step, n, flush=None, skip=0):
+    """Times ``n`` calls ``step(k)`` with a CUDA event pair each, all queued before the
+    first is read back, so that the device never waits for the host inside a timed
+    call; the L2 flush, when given, runs between the pairs.  Drops the first ``skip``."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        if flush is not None:
+            flush.fill_(float(k))
+        ev[k][0].record()
+        step(k)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev][skip:]
+
+
 def time_steps(torch, sv, steps, warmup, flush, profile=True, use_graph=True):
     for _ in range(warmup):
         flush.fill_(0.0)
@@ -291,6 +306,8 @@ def time_steps(torch, sv, steps, warmup, flush, profile=True, use_graph=True):
     if profile:
         sv.profile_read()
     times, pn, pms = [], 0, 0.0
+    if not profile:
+        return queued_times(torch, lambda k: sv.iterate(1, use_graph=use_graph), steps, flush), pn, pms
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for k in range(steps):
@@ -300,10 +317,9 @@ def time_steps(torch, sv, steps, warmup, flush, profile=True, use_graph=True):
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        if profile:
-            n, ms = sv.profile_read()
-            pn += n
-            pms += ms
+        n, ms = sv.profile_read()
+        pn += n
+        pms += ms
     return times, pn, pms
 
 
@@ -447,26 +463,15 @@ def operator_leg(torch, ops, g, dev, flush, hbm, steps=50, elem=4):
     r = [torch.randn(g.s, device=dev, dtype=dt) for _ in range(2)]
     d = [torch.empty(g.s, device=dev, dtype=dt) for _ in range(2)]
     a = [torch.empty(g.n, device=dev, dtype=dt) for _ in range(2)]
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     res = {}
     import paper_2112_15562_gb300 as gj
 
     for name in ("forward", "adjoint"):
-        ts = []
-        for k in range(steps + 3):
-            if flush is not None:
-                flush.fill_(float(k))
-            e0.record()
-            if name == "forward":
-                gj.g_forward_pair(ops, m, d)
-            else:
-                gj.g_adjoint_pair(ops, r, a)
-            e1.record()
-            e1.synchronize()
-            if k >= 3:
-                ts.append(e0.elapsed_time(e1))
-        res[name] = statistics.median(ts)
+        if name == "forward":
+            call = lambda k: gj.g_forward_pair(ops, m, d)  # noqa: E731
+        else:
+            call = lambda k: gj.g_adjoint_pair(ops, r, a)  # noqa: E731
+        res[name] = statistics.median(queued_times(torch, call, steps + 3, flush, skip=3))
     o = ops[0].info
     S_mag = o.nz * o.Ny * o.ncol * 2 * elem
     # per product: model and data vectors plus the layer spectra (the gravity spectrum
@@ -619,6 +624,42 @@ def c2_leg(gj, torch, dev, flush, hbm, steps=20):
                                  "256x256x40 line (spectrum bytes at the padded size in use)"}
 
 
+def c5_step(gj, ops, m, gd):
+    """One forward + backward of both fields through torch.autograd; the gradients are
+    cleared first, as an optimiser's zero_grad(set_to_none=True) does, so that no
+    accumulation kernel runs."""
+    for t in m:
+        t.grad = None
+    for i in range(2):
+        gj.G(ops[i], m[i]).backward(gd[i])
+
+
+def c5_graph(gj, torch, ops, m, gd, steps, flush, alg, hbm):
+    """The same forward + backward step captured once in a CUDA graph (torch.cuda.graph;
+    the library's products launch on the capturing stream) and replayed, so that the
+    step's time is the device's and not the host's issue of the autograd step; the
+    replayed gradients are compared with an eager step's."""
+    c5_step(gj, ops, m, gd)
+    ref = [t.grad.clone() for t in m]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            c5_step(gj, ops, m, gd)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        c5_step(gj, ops, m, gd)
+    graph.replay()
+    torch.cuda.synchronize()
+    err = max(float((t.grad - r).norm() / r.norm()) for t, r in zip(m, ref))
+    ts = queued_times(torch, lambda k: graph.replay(), steps + 1, flush, skip=1)
+    ms = statistics.median(ts)
+    del graph
+    return {"ms_per_fwd_bwd_both_fields": ms, "algorithmic_GBs": alg / (ms * 1e-3) / 1e9,
+            "frac_of_hbm": alg / (ms * 1e-3) / 1e9 / hbm, "grad_rel_diff_vs_eager": err}
+
+
 def c5_leg(gj, torch, dev, flush, hbm):
     """512x512 stations over 512x512x48 cells of 100 m (12.6 M cells per model), FP32,
     padded 1024 x 1024: forward plus backward (G m through torch.autograd, backward =
@@ -646,20 +687,7 @@ def c5_leg(gj, torch, dev, flush, hbm):
         t_setup = time.perf_counter() - t0
         m = [torch.rand(g.n, device=dev, requires_grad=True) for _ in range(2)]
         gd = [torch.randn(g.s, device=dev) for _ in range(2)]
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ts = []
-        for k in range(steps + 1):
-            flush.fill_(float(k))
-            for t in m:
-                t.grad = None  # as an optimiser's zero_grad(set_to_none=True): no accumulation kernel
-            e0.record()
-            for i in range(2):
-                gj.G(ops[i], m[i]).backward(gd[i])
-            e1.record()
-            e1.synchronize()
-            if k >= 1:
-                ts.append(e0.elapsed_time(e1))
+        ts = queued_times(torch, lambda k: c5_step(gj, ops, m, gd), steps + 1, flush, skip=1)
         ms = statistics.median(ts)
         o = ops[0].info
         S_mag = o.nz * o.Ny * o.ncol * 8
@@ -670,6 +698,11 @@ def c5_leg(gj, torch, dev, flush, hbm):
         if mode == "stored":
             res["algorithmic_GBs"] = alg / (ms * 1e-3) / 1e9
             res["frac_of_hbm"] = res["algorithmic_GBs"] / hbm
+            try:
+                res["graph"] = c5_graph(gj, torch, ops, m, gd, steps, flush, alg, hbm)
+            except Exception as exc:  # capture refused: the eager figure stands alone
+                torch.cuda.synchronize()
+                res["graph"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
         out[mode] = res
         for op in ops:
             op.close()
@@ -740,16 +773,7 @@ def batched_leg(gj, torch, dev, flush, steps=20, warmup=3):
     for _ in range(warmup):
         batch.step(1)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    ts = []
-    for k in range(steps):
-        flush.fill_(float(k))
-        e0.record()
-        batch.step(1)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
+    ts = queued_times(torch, lambda k: batch.step(1), steps, flush)
     batch.close()
     for s_ in solvers:
         s_.close()
@@ -859,19 +883,7 @@ def run_leg(args):
            gj.bttb_setup(g, "magnetic", mag, precision="fp32", npad=(1024, 1024))]
     m = [torch.rand(g.n, device=dev, requires_grad=True) for _ in range(2)]
     gd = [torch.randn(g.s, device=dev) for _ in range(2)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ts = []
-    for k in range(args.warmup + args.steps):
-        flush.fill_(float(k))
-        for t in m:
-            t.grad = None
-        e0.record()
-        for i in range(2):
-            gj.G(ops[i], m[i]).backward(gd[i])
-        e1.record()
-        e1.synchronize()
-        if k >= args.warmup:
-            ts.append(e0.elapsed_time(e1))
+    ts = queued_times(torch, lambda k: c5_step(gj, ops, m, gd), args.warmup + args.steps, flush, skip=args.warmup)
     print(json.dumps({"leg": "512x512x48 fwd+bwd of both fields, Npad 1024x1024, FP32",
                       "ms_per_fwd_bwd_both_fields": statistics.median(ts), "steps": args.steps}))
 

@@ -23,6 +23,9 @@
  *  - Errors: argument checks run synchronously and return a negative
  *    gj_status without enqueuing work; gj_last_error() then returns a message
  *    (per thread).  CUDA launch failures return GJ_ERR_CUDA.
+ *  - Kernel attributes (shared-memory limits) are set once per kernel and device
+ *    and kept for the life of the process; a caller that resets a device
+ *    (cudaDeviceReset) must not use the library on it afterwards.
  */
 #ifndef GJ_H
 #define GJ_H

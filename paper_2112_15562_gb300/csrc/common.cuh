@@ -3,6 +3,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace gj {
 
 template <typename R> struct CplxOf;
@@ -90,19 +94,32 @@ __device__ __forceinline__ void block_accumulate(const A *acc, double *out, doub
 // maximum less the kernel's static shared memory.  The attribute belongs to the
 // function, not to a launch, so setting it to the maximum keeps callers with
 // different sizes from overriding each other.
+// Done once per kernel and device: later calls return at once, so that a product's
+// launches cost no attribute queries on the host.
 template <typename F>
 inline cudaError_t allow_max_smem(F *f) {
-    static int optin = -1;
-    if (optin < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const std::pair<int, const void *> key{dev, reinterpret_cast<const void *>(f)};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (done.count(key)) return cudaSuccess;
     }
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 48 * 1024;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    e = cudaFuncGetAttributes(&fa, f);
     if (e != cudaSuccess) return e;
     const int dyn = optin - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn > 0 ? dyn : 0);
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn > 0 ? dyn : 0);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        done.insert(key);
+    }
+    return e;
 }
 
 }  // namespace gj
