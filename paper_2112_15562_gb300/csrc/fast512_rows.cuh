@@ -8,6 +8,45 @@ namespace gj {
 namespace f512 {
 
 // ---------------------------------------------------------------------------
+// Two fields' single-field products in one launch (the pair calls): a functor per
+// field, the one of field f taken with field_functor(pro, f).  Every other functor
+// serves its launch's lines as it is.
+template <typename R>
+struct LoadPlain2 {  // field f: lines la and lb of x[f]
+    const R *x[2];
+    int pitch;
+    static constexpr int NPRE = LoadPlain<R>::NPRE;
+    __device__ void init() {}
+    __device__ void flush(double *) const {}
+    __device__ LoadPlain<R> of(int f) const {  // a select, not an indexed load
+        const R *p = f ? x[1] : x[0];
+        return LoadPlain<R>{p, p, pitch};
+    }
+};
+template <typename R>
+struct StorePlain2 {  // field f: lines la and lb of y[f]
+    R *y[2];
+    int pitch;
+    static constexpr int NPRE = StorePlain<R>::NPRE;
+    __device__ void init() {}
+    __device__ void flush(double *) const {}
+    __device__ StorePlain<R> of(int f) const {  // a select, not an indexed load
+        R *p = f ? y[1] : y[0];
+        return StorePlain<R>{p, p, pitch};
+    }
+};
+template <class P>
+__device__ __forceinline__ P &field_functor(P &p, int) { return p; }
+template <typename R>
+__device__ __forceinline__ LoadPlain<R> field_functor(const LoadPlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ StorePlain<R> field_functor(const StorePlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ LoadPlain<R> field_functor(LoadPlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ StorePlain<R> field_functor(StorePlain2<R> &p, int f) { return p.of(f); }
+
+// ---------------------------------------------------------------------------
 // Row pass (x direction), real lines -> half spectra in the transposed layout.
 // A CTA of NW warps runs FPW complex transforms per warp (FFTS = NW * FPW per CTA).
 // Joint mode: transform f packs line (base + f) of field 0 (real part) and field 1
@@ -22,9 +61,10 @@ __device__ __forceinline__ void pair_lines(int joint, int base, int f, int nline
 
 // Splits the staged spectra of FFTS transforms into the two real half spectra and
 // writes them to out[r][kx][iy] (the transposed layout), iy fastest.
+// (single mode: the lines are field `field`'s)
 template <typename R, int FFTS>
 __device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const View2<R> &V, int joint, int base,
-                                                   int nlines, int lpl, int out_sel) {
+                                                   int nlines, int lpl, int out_sel, int field = 0) {
     using C = cpx<R>;
     static_assert((FFTS & (FFTS - 1)) == 0, "FFTS must be a power of two");
     // blockDim is a multiple of FFTS, so this thread always serves transform f
@@ -32,10 +72,10 @@ __device__ __forceinline__ void write_half_spectra(const cpx<R> *tile, const Vie
     int la, lb;
     bool ha, hb;
     pair_lines(joint, base, f, nlines, la, lb, ha, hb);
-    const int fb = joint ? 1 : 0;
+    const int fa = joint ? 0 : field, fb = joint ? 1 : field;
     const int ra = ha ? la / lpl : 0, rb = hb ? lb / lpl : 0;
     const int hy = V.hy;
-    C *oa = (out_sel == 0 ? V.op[0].Z : (out_sel == 1 ? V.op[0].W : V.op[0].V)) + (size_t)ra * NC * hy + (la - ra * lpl);
+    C *oa = (out_sel == 0 ? V.op[fa].Z : (out_sel == 1 ? V.op[fa].W : V.op[fa].V)) + (size_t)ra * NC * hy + (la - ra * lpl);
     C *ob = (out_sel == 0 ? V.op[fb].Z : (out_sel == 1 ? V.op[fb].W : V.op[fb].V)) + (size_t)rb * NC * hy + (lb - rb * lpl);
     const C *row = tile + f * (N + 1);
     const int kstep = blockDim.x / FFTS;
@@ -80,6 +120,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
     tw.load_fwd(V.op[0].twx);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15;
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
+    const int field = blockIdx.y;  // single mode: the field of this CTA's lines (grid y = fields)
     C *buf = xb + warp * N;
     for (int s = 0; s < FPW; ++s) {
         const int f = warp * FPW + s;
@@ -90,8 +131,8 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
         if (ha) {
             // two batches of four keep the prologue's registers below the spill point
             R a0[4], b0[4], a1[4], b1[4];
-            pro.template fetch_batch<4>(la, lb, hb, lane, 32, n_in, a0, b0);
-            pro.template fetch_batch<4>(la, lb, hb, lane + 128, 32, n_in, a1, b1);
+            field_functor(pro, field).template fetch_batch<4>(la, lb, hb, lane, 32, n_in, a0, b0);
+            field_functor(pro, field).template fetch_batch<4>(la, lb, hb, lane + 128, 32, n_in, a1, b1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
         } else {
@@ -105,7 +146,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
         for (int k1 = 0; k1 < 16; ++k1) tile[f * (N + 1) + ppos(lam + 32 * k1)] = v[k1];
     }
     __syncthreads();
-    write_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, out_sel);
+    write_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, out_sel, field);
     pro.flush(red);
 }
 
@@ -114,11 +155,11 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_fwd512(View2<R> V, int joint
 // The caller synchronises the block before reading the tile.
 template <typename R, int FFTS>
 __device__ __forceinline__ void stage_half_spectra(cpx<R> *tile, const View2<R> &V, int joint, int base, int nlines,
-                                                   int lpl, int in_sel) {
+                                                   int lpl, int in_sel, int field = 0) {
     using C = cpx<R>;
     constexpr int SRC = 2 * FFTS, P = SRC + 1;
     const int s = threadIdx.x % SRC;
-    const int fld = joint ? (s / FFTS) : 0;
+    const int fld = joint ? (s / FFTS) : field;
     const int line = joint ? base + (s % FFTS) : base + s;
     const bool ok = line < nlines;
     const int r = ok ? line / lpl : 0, iy = ok ? line - r * lpl : 0;
@@ -185,7 +226,8 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
     __shared__ double red[128];
     epi.init();
     const int base = blockIdx.x * (joint ? FFTS : 2 * FFTS);
-    stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel);
+    const int field = blockIdx.y;  // single mode: the field of this CTA's lines (grid y = fields)
+    stage_half_spectra<R, FFTS>(tile, V, joint, base, nlines, lpl, in_sel, field);
     __syncthreads();
     LaneTw<R> tw;
     tw.load_inv(V.op[0].twx);
@@ -198,15 +240,15 @@ __global__ void __launch_bounds__(NW * 32, 2) k_row_inv512(View2<R> V, int joint
         int la, lb;
         bool ha, hb;
         pair_lines(joint, base, f, nlines, la, lb, ha, hb);
-        if (ha) epi.prefetch(la, lb, hb, lane, n_out);  // the epilogue's rows load during the transform
+        if (ha) field_functor(epi, field).prefetch(la, lb, hb, lane, n_out);  // rows load during the transform
         R a[8], b[8];
         inv512_to_lines<R, FFTS>(tile, sa, sb, buf, tw, a, b);
         if (ha) {
             R a0[4], b0[4], a1[4], b1[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
-            epi.template store_batch<4>(la, lb, hb, lane, 32, n_out, a0, b0);
-            epi.template store_batch<4>(la, lb, hb, lane + 128, 32, n_out, a1, b1);
+            field_functor(epi, field).template store_batch<4>(la, lb, hb, lane, 32, n_out, a0, b0);
+            field_functor(epi, field).template store_batch<4>(la, lb, hb, lane + 128, 32, n_out, a1, b1);
         }
     }
     epi.flush(red);
@@ -416,19 +458,27 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, 
     LaneTw<R> tw;
     tw.load_fwd(V.op[0].twx);
     const int gpl = (lpl + LPG - 1) / LPG;
-    const long long NG = (long long)nz * gpl;
+    // pair mode with both fields in V: the groups of field 0, then those of field 1
+    const long long NG1 = (long long)nz * gpl;
+    const int nfl = (PAIR && V.nfield == 2) ? 2 : 1;
+    const long long NG = NG1 * nfl;
+    auto fgroup = [&](int q, int &f, int &r, int &iy0, int &ng) {
+        f = (nfl == 2 && q >= NG1) ? 1 : 0;
+        group_lines(q - (int)(f * NG1), gpl, lpl, LPG, r, iy0, ng);
+    };
     const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
     const long long tm = (long long)blockIdx.x * NT + team;
     if (tm < Tt) {
         const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         C *out0 = sel_buf(V.op[0], out_sel), *out1 = sel_buf(V.op[1], out_sel);
-        int r, iy0, ng, la, lb;
+        int fq, r, iy0, ng, la, lb;
         bool hb;
-        group_lines(q0, gpl, lpl, LPG, r, iy0, ng);
-        if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) prefetch_rows(pro, pre, la, hb ? lb : -1, n_in);
+        fgroup(q0, fq, r, iy0, ng);
+        if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb))
+            prefetch_rows(field_functor(pro, fq), pre, la, hb ? lb : -1, n_in);
         cp_async_commit();
         for (int q = q0; q < q1; ++q) {
-            group_lines(q, gpl, lpl, LPG, r, iy0, ng);
+            fgroup(q, fq, r, iy0, ng);
             C *tile = tiles + (q & 1) * 2 * FS;
             const bool act = warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb);  // this warp has a transform in q
             R a[8], b[8];
@@ -436,18 +486,18 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, 
                 cp_async_wait<0>();
                 __syncwarp();
                 R a0[4], b0[4], a1[4], b1[4];
-                pro.template fetch_batch<4, true>(la, lb, hb, lane, 32, n_in, a0, b0, pre);
-                pro.template fetch_batch<4, true>(la, lb, hb, lane + 128, 32, n_in, a1, b1, pre);
+                field_functor(pro, fq).template fetch_batch<4, true>(la, lb, hb, lane, 32, n_in, a0, b0, pre);
+                field_functor(pro, fq).template fetch_batch<4, true>(la, lb, hb, lane + 128, 32, n_in, a1, b1, pre);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { a[i] = a0[i]; b[i] = b0[i]; a[4 + i] = a1[i]; b[4 + i] = b1[i]; }
                 __syncwarp();
             }
             if (q + 1 < q1) {  // the rows of this warp's transform in the next group
-                int r2, iy2, ng2, la2, lb2;
+                int f2, r2, iy2, ng2, la2, lb2;
                 bool hb2;
-                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
+                fgroup(q + 1, f2, r2, iy2, ng2);
                 if (warp_lines<PAIR>(k, r2, iy2, ng2, lpl, la2, lb2, hb2))
-                    prefetch_rows(pro, pre, la2, hb2 ? lb2 : -1, n_in);
+                    prefetch_rows(field_functor(pro, f2), pre, la2, hb2 ? lb2 : -1, n_in);
             }
             cp_async_commit();
             if (act) {
@@ -458,7 +508,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_fwd512t(View2<R> V, int nz, 
             }
             team_barrier(team);  // the group's tile is complete; the other tile is free again
             const size_t off = (size_t)r * NC * V.hy + iy0;
-            team_store<R, PAIR>(tile, out0 + off, out1 + off, ng, tid, V.hy);
+            team_store<R, PAIR>(tile, (fq ? out1 : out0) + off, out1 + off, ng, tid, V.hy);
         }
     }
     pro.flush(red);
@@ -485,31 +535,39 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, 
     LaneTw<R> tw;
     tw.load_inv(V.op[0].twx);
     const int gpl = (lpl + LPG - 1) / LPG;
-    const long long NG = (long long)nz * gpl;
+    // pair mode with both fields in V: the groups of field 0, then those of field 1
+    const long long NG1 = (long long)nz * gpl;
+    const int nfl = (PAIR && V.nfield == 2) ? 2 : 1;
+    const long long NG = NG1 * nfl;
+    auto fgroup = [&](int q, int &f, int &r, int &iy0, int &ng) {
+        f = (nfl == 2 && q >= NG1) ? 1 : 0;
+        group_lines(q - (int)(f * NG1), gpl, lpl, LPG, r, iy0, ng);
+    };
     const long long Tt = seg_warps((long long)gridDim.x * NT, NG);
     const long long tm = (long long)blockIdx.x * NT + team;
     if (tm < Tt) {
         const int q0 = (int)seg_begin(tm, NG, Tt), q1 = (int)seg_begin(tm + 1, NG, Tt);
         const C *in0 = sel_buf(V.op[0], in_sel), *in1 = sel_buf(V.op[1], in_sel);
-        int r, iy0, ng, la, lb;
+        int fq, r, iy0, ng, la, lb;
         bool hb;
-        group_lines(q0, gpl, lpl, LPG, r, iy0, ng);
+        fgroup(q0, fq, r, iy0, ng);
         {
             const size_t off = (size_t)r * NC * V.hy + iy0;
-            team_load<R, PAIR>(tiles + (q0 & 1) * 2 * FS, in0 + off, in1 + off, ng, tid, V.hy);
+            team_load<R, PAIR>(tiles + (q0 & 1) * 2 * FS, (fq ? in1 : in0) + off, in1 + off, ng, tid, V.hy);
             cp_async_commit();
-            if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) prefetch_rows(epi, pre, la, hb ? lb : -1, n_out);
+            if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb))
+                prefetch_rows(field_functor(epi, fq), pre, la, hb ? lb : -1, n_out);
             cp_async_commit();
         }
         for (int q = q0; q < q1; ++q) {
-            group_lines(q, gpl, lpl, LPG, r, iy0, ng);
+            fgroup(q, fq, r, iy0, ng);
             cp_async_wait<1>();  // this thread's copies of the tile of q
             team_barrier(team);  // everyone's copies of q; the other tile is free again
             if (q + 1 < q1) {
-                int r2, iy2, ng2;
-                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
+                int f2, r2, iy2, ng2;
+                fgroup(q + 1, f2, r2, iy2, ng2);
                 const size_t off = (size_t)r2 * NC * V.hy + iy2;
-                team_load<R, PAIR>(tiles + ((q + 1) & 1) * 2 * FS, in0 + off, in1 + off, ng2, tid, V.hy);
+                team_load<R, PAIR>(tiles + ((q + 1) & 1) * 2 * FS, (f2 ? in1 : in0) + off, in1 + off, ng2, tid, V.hy);
             }
             cp_async_commit();
             if (warp_lines<PAIR>(k, r, iy0, ng, lpl, la, lb, hb)) {
@@ -522,16 +580,16 @@ __global__ void __launch_bounds__(NW * 32, 1) k_row_inv512t(View2<R> V, int nz, 
                 R a0[4], b0[4], a1[4], b1[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) { a0[i] = a[i]; b0[i] = b[i]; a1[i] = a[4 + i]; b1[i] = b[4 + i]; }
-                epi.template store_batch<4, true>(la, lb, hb, lane, 32, n_out, a0, b0, pre);
-                epi.template store_batch<4, true>(la, lb, hb, lane + 128, 32, n_out, a1, b1, pre);
+                field_functor(epi, fq).template store_batch<4, true>(la, lb, hb, lane, 32, n_out, a0, b0, pre);
+                field_functor(epi, fq).template store_batch<4, true>(la, lb, hb, lane + 128, 32, n_out, a1, b1, pre);
                 __syncwarp();
             }
             if (q + 1 < q1) {
-                int r2, iy2, ng2, la2, lb2;
+                int f2, r2, iy2, ng2, la2, lb2;
                 bool hb2;
-                group_lines(q + 1, gpl, lpl, LPG, r2, iy2, ng2);
+                fgroup(q + 1, f2, r2, iy2, ng2);
                 if (warp_lines<PAIR>(k, r2, iy2, ng2, lpl, la2, lb2, hb2))
-                    prefetch_rows(epi, pre, la2, hb2 ? lb2 : -1, n_out);
+                    prefetch_rows(field_functor(epi, f2), pre, la2, hb2 ? lb2 : -1, n_out);
             }
             cp_async_commit();
         }

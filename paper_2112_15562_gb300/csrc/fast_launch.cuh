@@ -58,19 +58,21 @@ inline void set_col_attr() {
 }
 
 // out_sel / in_sel: 0 = Z, 1 = W, 2 = V
+// nfield = 2 (single mode, with LoadPlain2 / StorePlain2): the lines of both fields,
+// grid y = field
 template <typename R, int NW, int FPW, class Pro>
 inline void row_fwd(const View2<R> &V, int joint, int nlines, int lpl, int n_in, int out_sel, const Pro &pro,
-                    const int *done, cudaStream_t st) {
+                    const int *done, cudaStream_t st, int nfield = 1) {
     const int per = (joint ? 1 : 2) * NW * FPW;
-    k_row_fwd512<R, Pro, NW, FPW><<<(nlines + per - 1) / per, NW * 32, smem_row_fwd<R, NW, FPW>(), st>>>(
+    k_row_fwd512<R, Pro, NW, FPW><<<dim3((nlines + per - 1) / per, nfield), NW * 32, smem_row_fwd<R, NW, FPW>(), st>>>(
         V, joint, nlines, lpl, n_in, out_sel, pro, done);
 }
 
 template <typename R, int NW, int FPW, class Epi>
 inline void row_inv(const View2<R> &V, int joint, int nlines, int lpl, int n_out, int in_sel, const Epi &epi,
-                    const int *done, cudaStream_t st) {
+                    const int *done, cudaStream_t st, int nfield = 1) {
     const int per = (joint ? 1 : 2) * NW * FPW;
-    k_row_inv512<R, Epi, NW, FPW><<<(nlines + per - 1) / per, NW * 32, smem_row_inv<R, NW, FPW>(), st>>>(
+    k_row_inv512<R, Epi, NW, FPW><<<dim3((nlines + per - 1) / per, nfield), NW * 32, smem_row_inv<R, NW, FPW>(), st>>>(
         V, joint, nlines, lpl, n_out, in_sel, epi, done);
 }
 

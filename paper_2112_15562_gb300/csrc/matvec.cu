@@ -206,30 +206,28 @@ static void fast_forward_pair(const gj_op *a, const gj_op *b, const float *m0, c
                               cudaStream_t st) {
     using namespace f512;
     View2<float> V = make_view2<float>(a, b);
-    View2<float> Va = make_view2<float>(a, nullptr), Vb = make_view2<float>(b, nullptr);
-    set_row_fwd_t_attr<float, LoadPlain<float>, true>();
-    set_row_inv_attr<float, StorePlain<float>, kDataNW, kDataFPW>();
+    set_row_fwd_t_attr<float, LoadPlain2<float>, true>();
+    set_row_inv_attr<float, StorePlain2<float>, kDataNW, kDataFPW>();
     set_col_attr<float>();
-    row_fwd_t<float, true>(Va, a->col_grid, a->nz, a->ny, a->nx, 0, LoadPlain<float>{m0, m0, a->nx}, nullptr, st);
-    row_fwd_t<float, true>(Vb, b->col_grid, b->nz, b->ny, b->nx, 0, LoadPlain<float>{m1, m1, b->nx}, nullptr, st);
+    // one launch per pass: the row passes take both fields' lines (pair mode, each
+    // field's functor), the column pass both fields' columns
+    row_fwd_t<float, true>(V, a->col_grid, a->nz, a->ny, a->nx, 0, LoadPlain2<float>{{m0, m1}, a->nx}, nullptr, st);
     col_fwd<float>(V, a->col_grid, nullptr, st);
-    row_inv<float, kDataNW, kDataFPW>(Va, 0, a->sy, a->sy, a->sx, 1, StorePlain<float>{d0, d0, a->sx}, nullptr, st);
-    row_inv<float, kDataNW, kDataFPW>(Vb, 0, b->sy, b->sy, b->sx, 1, StorePlain<float>{d1, d1, b->sx}, nullptr, st);
+    row_inv<float, kDataNW, kDataFPW>(V, 0, a->sy, a->sy, a->sx, 1, StorePlain2<float>{{d0, d1}, a->sx}, nullptr, st,
+                                      2);
 }
 
 static void fast_adjoint_pair(const gj_op *a, const gj_op *b, const float *r0, const float *r1, float *g0, float *g1,
                               cudaStream_t st) {
     using namespace f512;
     View2<float> V = make_view2<float>(a, b);
-    View2<float> Va = make_view2<float>(a, nullptr), Vb = make_view2<float>(b, nullptr);
-    set_row_fwd_attr<float, LoadPlain<float>, kDataNW, kDataFPW>();
-    set_row_inv_t_attr<float, StorePlain<float>, true>();
+    set_row_fwd_attr<float, LoadPlain2<float>, kDataNW, kDataFPW>();
+    set_row_inv_t_attr<float, StorePlain2<float>, true>();
     set_col_attr<float>();
-    row_fwd<float, kDataNW, kDataFPW>(Va, 0, a->sy, a->sy, a->sx, 2, LoadPlain<float>{r0, r0, a->sx}, nullptr, st);
-    row_fwd<float, kDataNW, kDataFPW>(Vb, 0, b->sy, b->sy, b->sx, 2, LoadPlain<float>{r1, r1, b->sx}, nullptr, st);
+    row_fwd<float, kDataNW, kDataFPW>(V, 0, a->sy, a->sy, a->sx, 2, LoadPlain2<float>{{r0, r1}, a->sx}, nullptr, st,
+                                      2);
     col_adj<float>(V, a->col_grid, nullptr, st);
-    row_inv_t<float, true>(Va, a->col_grid, a->nz, a->ny, a->nx, 0, StorePlain<float>{g0, g0, a->nx}, nullptr, st);
-    row_inv_t<float, true>(Vb, b->col_grid, b->nz, b->ny, b->nx, 0, StorePlain<float>{g1, g1, b->nx}, nullptr, st);
+    row_inv_t<float, true>(V, a->col_grid, a->nz, a->ny, a->nx, 0, StorePlain2<float>{{g0, g1}, a->nx}, nullptr, st);
 }
 
 // Two operators serve one joint launch when both are on the fast path with the same
