@@ -393,4 +393,43 @@ struct StorePlain {
     __device__ __forceinline__ void flush(double *) const {}
 };
 
+// ---------------------------------------------------------------------------
+// Two fields' single-field products in one launch (the pair calls): a functor per
+// field, the one of field f taken with field_functor(pro, f).  Every other functor
+// serves its launch's lines as it is.
+template <typename R>
+struct LoadPlain2 {  // field f: lines la and lb of x[f]
+    const R *x[2];
+    int pitch;
+    static constexpr int NPRE = LoadPlain<R>::NPRE;
+    __device__ void init() {}
+    __device__ void flush(double *) const {}
+    __device__ LoadPlain<R> of(int f) const {  // a select, not an indexed load
+        const R *p = f ? x[1] : x[0];
+        return LoadPlain<R>{p, p, pitch};
+    }
+};
+template <typename R>
+struct StorePlain2 {  // field f: lines la and lb of y[f]
+    R *y[2];
+    int pitch;
+    static constexpr int NPRE = StorePlain<R>::NPRE;
+    __device__ void init() {}
+    __device__ void flush(double *) const {}
+    __device__ StorePlain<R> of(int f) const {  // a select, not an indexed load
+        R *p = f ? y[1] : y[0];
+        return StorePlain<R>{p, p, pitch};
+    }
+};
+template <class P>
+__device__ __forceinline__ P &field_functor(P &p, int) { return p; }
+template <typename R>
+__device__ __forceinline__ LoadPlain<R> field_functor(const LoadPlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ StorePlain<R> field_functor(const StorePlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ LoadPlain<R> field_functor(LoadPlain2<R> &p, int f) { return p.of(f); }
+template <typename R>
+__device__ __forceinline__ StorePlain<R> field_functor(StorePlain2<R> &p, int f) { return p.of(f); }
+
 }  // namespace gj

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_fwd1024(OpView<R> op, PairMa
         for (int i = 0; i < 16; ++i) {
             const int e = lane + 32 * i;
             a[i] = b[i] = R(0);
-            if (e < n_in) pro.fetch(la, lb, hb, e, a[i], b[i]);
+            if (e < n_in) field_functor(pro, blockIdx.y).fetch(la, lb, hb, e, a[i], b[i]);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) buf[lane + 32 * i] = mk<C>(a[i], b[i]);
@@ -537,6 +537,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_fwd1024(OpView<R> op, PairMa
         const int s = threadIdx.x % RSLOT;
         int line, field;
         if (slot_line(pm, base, s, line, field)) {
+            if (!pm.joint) field = blockIdx.y;  // pairs of one field: the launch's grid y
             C *o = (field ? out1 : out0) + pm.at(line, 0, op.ncol, op.tcol);
             const size_t step = op.tcol ? (size_t)op.tcol : 1;
             for (int k = threadIdx.x / RSLOT; k < NCR; k += blockDim.x / RSLOT) o[k * step] = tile[s * TP + k];
@@ -562,6 +563,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_inv1024(OpView<R> op, PairMa
         const int s = threadIdx.x % RSLOT;
         int line, field;
         const bool ok = slot_line(pm, base, s, line, field);
+        if (!pm.joint) field = blockIdx.y;  // pairs of one field: the launch's grid y
         const C *src = ok ? (field ? in1 : in0) + pm.at(line, 0, op.ncol, op.tcol) : nullptr;
         const size_t step = op.tcol ? (size_t)op.tcol : 1;
         // every copy of the CTA's half spectra in flight at once (asynchronous copies)
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(RW * 32, 2) k_row_inv1024(OpView<R> op, PairMa
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
             const int n = l + 16 * (16 * h + jj);
-            if (n < n_out) epi.store(la, lb, hb, n, out[jj].x, out[jj].y);
+            if (n < n_out) field_functor(epi, blockIdx.y).store(la, lb, hb, n, out[jj].x, out[jj].y);
         }
     }
     epi.flush(red);

@@ -143,17 +143,19 @@ inline int row_grid(const PairMap &pm) {
     const int np = pm.joint ? pm.nlines : (pm.nlines + 1) / 2;
     return (np + RW - 1) / RW;
 }
+// nfield = 2 (pairs of one field's lines, LoadPlain2 / StorePlain2): both fields in one
+// launch, grid y = field, field 1's buffers in o1 / i1
 template <typename R, class Pro>
 inline void row_fwd(const OpView<R> &v, const PairMap &pm, int n_in, cpx<R> *o0, cpx<R> *o1, const void *tab,
-                    const Pro &pro, const int *done, cudaStream_t st) {
-    k_row_fwd1024<R, Pro><<<row_grid(pm), RW * 32, smem_row<R>(), st>>>(v, pm, n_in, o0, o1,
-                                                                        static_cast<const cpx<R> *>(tab), pro, done);
+                    const Pro &pro, const int *done, cudaStream_t st, int nfield = 1) {
+    k_row_fwd1024<R, Pro><<<dim3(row_grid(pm), nfield), RW * 32, smem_row<R>(), st>>>(
+        v, pm, n_in, o0, o1, static_cast<const cpx<R> *>(tab), pro, done);
 }
 template <typename R, class Epi>
 inline void row_inv(const OpView<R> &v, const PairMap &pm, int n_out, const cpx<R> *i0, const cpx<R> *i1,
-                    const void *tab, const Epi &epi, const int *done, cudaStream_t st) {
-    k_row_inv1024<R, Epi><<<row_grid(pm), RW * 32, smem_row<R>(), st>>>(v, pm, n_out, i0, i1,
-                                                                        static_cast<const cpx<R> *>(tab), epi, done);
+                    const void *tab, const Epi &epi, const int *done, cudaStream_t st, int nfield = 1) {
+    k_row_inv1024<R, Epi><<<dim3(row_grid(pm), nfield), RW * 32, smem_row<R>(), st>>>(
+        v, pm, n_out, i0, i1, static_cast<const cpx<R> *>(tab), epi, done);
 }
 
 }  // namespace f1024

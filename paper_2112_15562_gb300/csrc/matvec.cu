@@ -68,6 +68,18 @@ static void fast1024_forward(const gj_op *a, const gj_op *b, const float *m0, co
     const float *ms[2] = {m0, m1};
     float *ds[2] = {d0, d1};
     const int nf = b ? 2 : 1;
+    if (rows1024 && nf == 2) {
+        // both fields' row passes in one launch each (grid y = field)
+        f1024::set_row_fwd_attr<R, LoadPlain2<R>>();
+        f1024::set_row_inv_attr<R, StorePlain2<R>>();
+        OpView<R> va = view_of<R>(a), vb = view_of<R>(b);
+        PairMap pm{a->nz * a->ny, 0, a->ny};
+        f1024::row_fwd<R>(va, pm, a->nx, va.Z, vb.Z, a->twtab, LoadPlain2<R>{{m0, m1}, a->nx}, nullptr, st, 2);
+        f1024::col_fwd<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
+        PairMap ps{a->sy, 0, a->sy};
+        f1024::row_inv<R>(va, ps, a->sx, va.W, vb.W, a->twtab, StorePlain2<R>{{d0, d1}, a->sx}, nullptr, st, 2);
+        return;
+    }
     for (int i = 0; i < nf; ++i) {
         const gj_op *o = ops[i];
         OpView<R> v = view_of<R>(o);
@@ -111,6 +123,18 @@ static void fast1024_adjoint(const gj_op *a, const gj_op *b, const float *r0, co
     const float *rs[2] = {r0, r1};
     float *gs[2] = {g0, g1};
     const int nf = b ? 2 : 1;
+    if (rows1024 && nf == 2) {
+        // both fields' row passes in one launch each (grid y = field)
+        f1024::set_row_fwd_attr<R, LoadPlain2<R>>();
+        f1024::set_row_inv_attr<R, StorePlain2<R>>();
+        OpView<R> va = view_of<R>(a), vb = view_of<R>(b);
+        PairMap ps{a->sy, 0, a->sy};
+        f1024::row_fwd<R>(va, ps, a->sx, va.V, vb.V, a->twtab, LoadPlain2<R>{{r0, r1}, a->sx}, nullptr, st, 2);
+        f1024::col_adj<R>(f512::make_view2<R>(a, b), a->col_grid, nullptr, st);
+        PairMap pm{a->nz * a->ny, 0, a->ny};
+        f1024::row_inv<R>(va, pm, a->nx, va.Z, vb.Z, a->twtab, StorePlain2<R>{{g0, g1}, a->nx}, nullptr, st, 2);
+        return;
+    }
     for (int i = 0; i < nf; ++i) {
         const gj_op *o = ops[i];
         OpView<R> v = view_of<R>(o);
